@@ -1,0 +1,168 @@
+/*
+ * libh2 -- minimal-rank H^2 matrix-vector product and Krylov solve on one GPU.
+ *
+ * The operator is the H^2 representation of a dense complex matrix A
+ * (Omar & Jiao, Sec. III.C, Eqs. 8-9, and Sec. IV.A):
+ *
+ *   A = sum over near (inadmissible leaf) blocks        Z^{t,s}
+ *     + sum over admissible blocks (t,s)   U^t S^{t,s} W^{sT}
+ *
+ * with nested cluster bases U^t = [U^{t1} T^{t1}; U^{t2} T^{t2}] and
+ * W^t = [W^{t1} T^{t1}; W^{t2} T^{t2}] for a non-leaf t with children t1, t2
+ * (Eq. 9). W = U gives the paper's symmetric form V^t S V^{sT} (Eq. 8).
+ *
+ * Conventions of every entry point:
+ *   - complex numbers are interleaved (re, im): "c64" = two floats,
+ *     "c128" = two doubles;
+ *   - all matrices are column-major; all vectors are in tree order, i.e.
+ *     every cluster is a contiguous index range [begin, begin + size);
+ *   - host arrays passed to h2_load are owned by the caller and copied; every
+ *     device buffer behind a handle is owned by the library;
+ *   - vectors passed to h2_matvec / h2_gmres are caller-owned DEVICE
+ *     pointers, except in the *_host variants, which take host pointers;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); all work is ordered on that stream;
+ *   - no call exits, traps or prints; failures are returned as h2_status and
+ *     the handle stays usable unless the status is H2_ERR_CUDA.
+ */
+#ifndef LIBH2_H2_H
+#define LIBH2_H2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    H2_OK = 0,
+    H2_ERR_ARG = 1,            /* invalid argument, shape or inconsistent tree/partition */
+    H2_ERR_ALLOC = 2,          /* device or host allocation failed */
+    H2_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    H2_ERR_NOT_CONVERGED = 4,  /* Krylov solve hit maxit before tol */
+    H2_ERR_BREAKDOWN = 5,      /* Krylov breakdown or non-finite values */
+    H2_ERR_TIMEOUT = 6,        /* a bounded device wait ran out */
+    H2_ERR_STATE = 7           /* call not valid in the handle's state */
+} h2_status;
+
+typedef enum { H2_C64 = 0, H2_C128 = 1 } h2_dtype;
+
+typedef enum {
+    H2_PREC_FP32 = 0,      /* c64 vectors, FP32 products and accumulation */
+    H2_PREC_SPLITBF16 = 1, /* c64 vectors; multi-RHS products on tensor cores
+                              with operands split into two bf16 terms */
+    H2_PREC_FP64ACC = 2    /* c128 vectors, stored FP32 data, FP64 accumulation */
+} h2_prec;
+
+typedef struct h2_handle h2_handle;
+
+/*
+ * Binary cluster tree (Sec. III.A), clusters numbered in breadth-first
+ * (level) order: cluster 0 is the root and covers [0, n); the clusters of
+ * level l are [level_ptr[l], level_ptr[l+1]).
+ */
+typedef struct {
+    int32_t n;                /* number of unknowns N > 0 */
+    int32_t n_clusters;       /* number of clusters */
+    int32_t n_levels;         /* number of levels */
+    const int32_t *level_ptr; /* [n_levels + 1] */
+    const int32_t *child;     /* [2 * n_clusters]: children of t at 2t, 2t+1; -1, -1 for a leaf */
+    const int32_t *begin;     /* [n_clusters]: first unknown of each cluster */
+    const int32_t *size;      /* [n_clusters]: number of unknowns, > 0 */
+    const int32_t *rank;      /* [n_clusters]: rank k_t >= 0 of the cluster basis */
+} h2_tree;
+
+/*
+ * Blocks of the H^2 representation. Every *_off array holds ELEMENT offsets
+ * (complex elements, not bytes) into the matching data array, whose total
+ * length in elements is *_len; entries for clusters that have no such block
+ * are ignored. Elements are c64 or c128 according to `dtype`.
+ */
+typedef struct {
+    h2_dtype dtype;
+    /* leaf row bases U^t (n_t x k_t), Eqs. 11-12; indexed by cluster */
+    const void *U; const int64_t *U_off; int64_t U_len;
+    /* leaf column bases W^t (n_t x k_t); W == NULL means W = U */
+    const void *W; const int64_t *W_off; int64_t W_len;
+    /* transfer T^t (k_t x k_parent) of every non-root cluster t, Eq. 16 */
+    const void *T; const int64_t *T_off; int64_t T_len;
+    /* admissible blocks, row-cluster CSR: the partners of t are
+       adm_col[adm_ptr[t] .. adm_ptr[t+1]); coupling S^{t,s} (k_t x k_s)
+       at S_off[j] for the j-th entry, Eq. 18 */
+    const int32_t *adm_ptr; const int32_t *adm_col;
+    const void *S; const int64_t *S_off; int64_t S_len;
+    /* near-field (inadmissible) blocks between leaves, same CSR form;
+       Z^{t,s} (n_t x n_s) at Z_off[j] */
+    const int32_t *near_ptr; const int32_t *near_col;
+    const void *Z; const int64_t *Z_off; int64_t Z_len;
+} h2_data;
+
+/*
+ * Validate a tree and its block partition, re-pack the blocks into the
+ * device layout (FP32 complex) and upload them. Checks: tree shape and
+ * index ranges, rank bounds (leaf k_t <= n_t, non-leaf k_t <= k_t1 + k_t2),
+ * offsets within *_len, near blocks only between leaves, and that the
+ * admissible and near blocks tile the N x N index square exactly once.
+ * The upload is synchronous. On success *out receives a new handle; on
+ * failure *out is set to NULL and nothing is leaked.
+ * `opts` may be NULL or a string of "key=value" pairs separated by ';'
+ * (currently: "device=<int>").
+ */
+h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
+                  h2_handle **out);
+
+/* Release every device and host resource of the handle (NULL is ignored).
+   Synchronises the handle's internal streams first. */
+void h2_free(h2_handle *h);
+
+/*
+ * y = A x for nrhs right-hand sides (Sec. IV.B): forward transformation,
+ * coupling multiplication, backward transformation, plus the full products
+ * with the inadmissible blocks. x and y are device arrays of nrhs columns of
+ * length N with leading dimension ld >= N (elements); y is overwritten and
+ * must not overlap x. Element type: c64 for H2_PREC_FP32 / H2_PREC_SPLITBF16,
+ * c128 for H2_PREC_FP64ACC. nrhs >= 1. H2_PREC_SPLITBF16 requires nrhs >= 2.
+ * Asynchronous on `stream`. Not thread-safe on one handle.
+ */
+h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs,
+                    int64_t ld, h2_prec prec, void *stream);
+
+/* As h2_matvec, but x and y are HOST arrays: the call copies x to the device,
+   runs the product and copies y back, and returns when y is complete. */
+h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host,
+                         int32_t nrhs, int64_t ld, h2_prec prec);
+
+/* Sizes of the loaded representation (all counts in complex elements). */
+typedef struct {
+    int64_t n, n_clusters, n_leaves, n_levels;
+    int64_t near_blocks, adm_blocks;
+    int64_t near_elems;      /* sum of n_t n_s over near blocks */
+    int64_t coupling_elems;  /* sum of k_t k_s over admissible blocks */
+    int64_t transfer_elems;  /* sum of k_t k_parent over non-root clusters */
+    int64_t leaf_elems;      /* sum of n_t k_t over leaves */
+    int64_t device_bytes;    /* device memory held by the handle */
+    int32_t max_rank;
+} h2_stats;
+
+h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
+
+/*
+ * Time the stages of a single-RHS FP32 product with CUDA events recorded on
+ * the stream each stage is launched on. x, y: device c64 vectors. Runs `iters`
+ * products (after one warm-up) and writes the mean duration in milliseconds
+ * of each stage to ms[0..n_ms) in the order: near field, leaf forward,
+ * upward transfers, coupling + downward transfers, leaf expansion, whole
+ * product. Synchronous.
+ */
+h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
+                            double *ms, int32_t n_ms);
+
+const char *h2_status_string(h2_status s);
+
+/* Text of the last CUDA or validation error seen by this thread ("" if none). */
+const char *h2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBH2_H2_H */

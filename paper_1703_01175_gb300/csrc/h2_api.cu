@@ -1,0 +1,679 @@
+// libh2 C ABI: loading (validation + re-packing), products, statistics.
+//
+// h2_load turns the caller's tree, bases, transfers, couplings and near
+// blocks (Sec. III.C, Sec. IV.A) into the task lists executed by the
+// block-row GEMV kernels. The device layout is:
+//   mat   one float2 array holding every task's column-major matrix,
+//         each starting on a 256-byte boundary, rows padded to even;
+//   coef  2 * sum(k_t) coefficients: xh^t at xo[t], yh^t at ktot + xo[t];
+//   tasks/segs  the task and input-segment descriptors of every phase.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+#define H2_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e__ = (call);                                                         \
+        if (e__ != cudaSuccess) {                                                         \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));               \
+            return H2_ERR_CUDA;                                                           \
+        }                                                                                 \
+    } while (0)
+
+static h2_status arg_error(const std::string &msg)
+{
+    set_error(msg);
+    return H2_ERR_ARG;
+}
+
+// read complex element i of a c64 / c128 host array
+struct CplxIn {
+    const void *p;
+    h2_dtype dt;
+    inline float2 at(int64_t i) const
+    {
+        if (dt == H2_C64) return reinterpret_cast<const float2 *>(p)[i];
+        const double2 v = reinterpret_cast<const double2 *>(p)[i];
+        return make_float2((float)v.x, (float)v.y);
+    }
+};
+
+static int choose_threads(const std::vector<Task> &tasks)
+{
+    static const int cand[] = {128, 192, 256, 384, 512, 768, 1024};
+    int maxP = 1;
+    double total = 0;
+    for (const Task &t : tasks) {
+        maxP = std::max(maxP, t.mpad / 2);
+        total += (double)t.mpad * t.ncol;
+    }
+    int best = 1024;
+    double best_score = -1e30;
+    for (int T : cand) {
+        if (T < maxP) continue;
+        double eff = 0;
+        for (const Task &t : tasks) {
+            const int P = t.mpad / 2;
+            eff += (double)t.mpad * t.ncol * (double)((T / P) * P) / T;
+        }
+        eff = total > 0 ? eff / total : 1.0;
+        // prefer full thread utilisation, then 256-512 thread CTAs
+        const double score = eff - 0.03 * std::fabs(std::log2((double)T / 384.0));
+        if (score > best_score) {
+            best_score = score;
+            best = T;
+        }
+    }
+    return best;
+}
+
+}  // namespace h2
+
+using namespace h2;
+
+static h2_status validate_tree(const h2_tree *tr, std::vector<int32_t> &parent,
+                               std::vector<int32_t> &level)
+{
+    if (!tr) return arg_error("tree is NULL");
+    const int32_t n = tr->n, nc = tr->n_clusters, nl = tr->n_levels;
+    if (n <= 0 || nc <= 0 || nl <= 0) return arg_error("tree: n, n_clusters and n_levels must be > 0");
+    if (!tr->level_ptr || !tr->child || !tr->begin || !tr->size || !tr->rank)
+        return arg_error("tree: NULL array");
+    if (tr->level_ptr[0] != 0 || tr->level_ptr[nl] != nc) return arg_error("tree: level_ptr must span [0, n_clusters]");
+    if (tr->level_ptr[1] != 1) return arg_error("tree: level 0 must hold only the root");
+    parent.assign(nc, -1);
+    level.assign(nc, -1);
+    for (int l = 0; l < nl; ++l) {
+        if (tr->level_ptr[l + 1] < tr->level_ptr[l]) return arg_error("tree: level_ptr not monotone");
+        for (int t = tr->level_ptr[l]; t < tr->level_ptr[l + 1]; ++t) level[t] = l;
+    }
+    if (tr->begin[0] != 0 || tr->size[0] != n) return arg_error("tree: root must cover [0, n)");
+    for (int t = 0; t < nc; ++t) {
+        if (tr->size[t] <= 0) return arg_error("tree: cluster sizes must be > 0");
+        if (tr->rank[t] < 0) return arg_error("tree: negative rank");
+        const int32_t c1 = tr->child[2 * t], c2 = tr->child[2 * t + 1];
+        if ((c1 < 0) != (c2 < 0)) return arg_error("tree: a cluster must have 0 or 2 children");
+        if (c1 < 0) {
+            if (tr->rank[t] > tr->size[t]) return arg_error("tree: leaf rank exceeds leaf size");
+            if (tr->size[t] > 2048) return arg_error("tree: leaf size above 2048");
+            continue;
+        }
+        if (c1 >= nc || c2 >= nc || c1 == c2) return arg_error("tree: child index out of range");
+        if (parent[c1] != -1 || parent[c2] != -1 || c1 == 0 || c2 == 0)
+            return arg_error("tree: a cluster has two parents");
+        parent[c1] = t;
+        parent[c2] = t;
+        if (level[c1] != level[t] + 1 || level[c2] != level[t] + 1)
+            return arg_error("tree: children must be on the next level");
+        if (tr->begin[c1] != tr->begin[t] || tr->begin[c2] != tr->begin[c1] + tr->size[c1] ||
+            tr->size[c1] + tr->size[c2] != tr->size[t])
+            return arg_error("tree: children must split the parent's range in order");
+        if (tr->rank[t] > tr->rank[c1] + tr->rank[c2])
+            return arg_error("tree: non-leaf rank exceeds the sum of its children's ranks");
+    }
+    for (int t = 1; t < nc; ++t)
+        if (parent[t] < 0) return arg_error("tree: cluster without parent");
+    for (int t = 0; t < nc; ++t)
+        if (tr->rank[t] > 2048) return arg_error("tree: rank above 2048");
+    return H2_OK;
+}
+
+static h2_status validate_data(const h2_tree *tr, const h2_data *d, const std::vector<int32_t> &parent)
+{
+    if (!d) return arg_error("data is NULL");
+    if (d->dtype != H2_C64 && d->dtype != H2_C128) return arg_error("data: bad dtype");
+    const int32_t nc = tr->n_clusters, n = tr->n;
+    auto leaf = [&](int t) { return tr->child[2 * t] < 0; };
+    bool any_rank = false;
+    for (int t = 0; t < nc; ++t) any_rank |= tr->rank[t] > 0;
+    if (any_rank && (!d->U || !d->U_off)) return arg_error("data: U missing");
+    for (int t = 0; t < nc; ++t) {
+        const int64_t k = tr->rank[t], nt = tr->size[t];
+        if (leaf(t) && k > 0) {
+            if (d->U_off[t] < 0 || d->U_off[t] + nt * k > d->U_len) return arg_error("data: U block out of range");
+            if (d->W) {
+                if (!d->W_off) return arg_error("data: W_off missing");
+                if (d->W_off[t] < 0 || d->W_off[t] + nt * k > d->W_len) return arg_error("data: W block out of range");
+            }
+        }
+        if (t > 0 && k > 0 && tr->rank[parent[t]] > 0) {
+            if (!d->T || !d->T_off) return arg_error("data: T missing");
+            const int64_t kp = tr->rank[parent[t]];
+            if (d->T_off[t] < 0 || d->T_off[t] + k * kp > d->T_len) return arg_error("data: T block out of range");
+        }
+    }
+    if (!d->adm_ptr || !d->near_ptr || !d->near_col || !d->Z || !d->Z_off)
+        return arg_error("data: CSR arrays missing");
+    if (d->adm_ptr[0] != 0 || d->near_ptr[0] != 0) return arg_error("data: CSR must start at 0");
+    for (int t = 0; t < nc; ++t) {
+        if (d->adm_ptr[t + 1] < d->adm_ptr[t] || d->near_ptr[t + 1] < d->near_ptr[t])
+            return arg_error("data: CSR pointers not monotone");
+        for (int j = d->adm_ptr[t]; j < d->adm_ptr[t + 1]; ++j) {
+            const int s = d->adm_col[j];
+            if (s < 0 || s >= nc) return arg_error("data: admissible column out of range");
+            const int64_t kk = (int64_t)tr->rank[t] * tr->rank[s];
+            if (kk > 0 && (!d->S || !d->S_off || d->S_off[j] < 0 || d->S_off[j] + kk > d->S_len))
+                return arg_error("data: S block out of range");
+        }
+        if (d->near_ptr[t + 1] > d->near_ptr[t] && !leaf(t)) return arg_error("data: near block on a non-leaf row");
+        for (int j = d->near_ptr[t]; j < d->near_ptr[t + 1]; ++j) {
+            const int s = d->near_col[j];
+            if (s < 0 || s >= nc || !leaf(s)) return arg_error("data: near column is not a leaf");
+            const int64_t nn = (int64_t)tr->size[t] * tr->size[s];
+            if (d->Z_off[j] < 0 || d->Z_off[j] + nn > d->Z_len) return arg_error("data: Z block out of range");
+        }
+    }
+    // the blocks covering the rows of each leaf must tile [0, n) exactly once
+    std::vector<std::pair<int32_t, int32_t>> iv;
+    for (int t = 0; t < nc; ++t) {
+        if (!leaf(t)) continue;
+        iv.clear();
+        for (int j = d->near_ptr[t]; j < d->near_ptr[t + 1]; ++j) {
+            const int s = d->near_col[j];
+            iv.emplace_back(tr->begin[s], tr->size[s]);
+        }
+        for (int a = t; a >= 0; a = parent[a])
+            for (int j = d->adm_ptr[a]; j < d->adm_ptr[a + 1]; ++j) {
+                const int s = d->adm_col[j];
+                iv.emplace_back(tr->begin[s], tr->size[s]);
+            }
+        std::sort(iv.begin(), iv.end());
+        int64_t pos = 0;
+        for (auto &p : iv) {
+            if (p.first != pos) return arg_error("data: blocks do not tile the matrix exactly once");
+            pos += p.second;
+        }
+        if (pos != n) return arg_error("data: blocks do not tile the matrix exactly once");
+    }
+    return H2_OK;
+}
+
+extern "C" {
+
+const char *h2_status_string(h2_status s)
+{
+    switch (s) {
+        case H2_OK: return "ok";
+        case H2_ERR_ARG: return "invalid argument";
+        case H2_ERR_ALLOC: return "allocation failed";
+        case H2_ERR_CUDA: return "CUDA error";
+        case H2_ERR_NOT_CONVERGED: return "not converged";
+        case H2_ERR_BREAKDOWN: return "breakdown";
+        case H2_ERR_TIMEOUT: return "timeout";
+        case H2_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *h2_last_error(void) { return g_last_error.c_str(); }
+
+void h2_free(h2_handle *h)
+{
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->s_aux) cudaStreamSynchronize(h->s_aux);
+    cudaDeviceSynchronize();
+    cudaFree(h->d_mat);
+    cudaFree(h->d_segs);
+    cudaFree(h->d_tasks);
+    cudaFree(h->d_coef);
+    cudaFree(h->d_xbuf);
+    cudaFree(h->d_ybuf);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_near) cudaEventDestroy(h->ev_near);
+    if (h->s_aux) cudaStreamDestroy(h->s_aux);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out)
+{
+    if (!out) return arg_error("out is NULL");
+    *out = nullptr;
+    std::vector<int32_t> parent, level;
+    h2_status st = validate_tree(tree, parent, level);
+    if (st != H2_OK) return st;
+    st = validate_data(tree, data, parent);
+    if (st != H2_OK) return st;
+
+    int device = 0;
+    if (opts) {
+        const char *p = strstr(opts, "device=");
+        if (p) device = atoi(p + 7);
+    }
+    h2_handle *h = new (std::nothrow) h2_handle();
+    if (!h) return H2_ERR_ALLOC;
+    h->device = device;
+    const int32_t n = tree->n, nc = tree->n_clusters, nl = tree->n_levels;
+    h->n = n;
+    h->nc = nc;
+    h->nlev = nl;
+    h->level_ptr.assign(tree->level_ptr, tree->level_ptr + nl + 1);
+    h->child.assign(tree->child, tree->child + 2 * nc);
+    h->begin.assign(tree->begin, tree->begin + nc);
+    h->size.assign(tree->size, tree->size + nc);
+    h->rank.assign(tree->rank, tree->rank + nc);
+    h->parent = parent;
+    h->level = level;
+    h->xo.assign(nc, 0);
+    int64_t ktot = 0;
+    for (int t = 0; t < nc; ++t) {
+        h->xo[t] = (int32_t)ktot;
+        ktot += tree->rank[t];
+    }
+    h->ktot = ktot;
+    if (2 * ktot + 2 * (int64_t)n > INT32_MAX) {
+        delete h;
+        return arg_error("problem too large for 32-bit offsets");
+    }
+    auto leaf = [&](int t) { return tree->child[2 * t] < 0; };
+    auto enc1 = [](int64_t off) { return (int32_t)(-off - 1); };
+    const int32_t *rk = tree->rank;
+
+    // ---- build the task lists --------------------------------------------------
+    struct Piece {
+        int kind;  // 0 Z, 1 U, 2 W, 3 T, 4 S
+        int64_t off;
+        int32_t rows, cols;  // source block shape (column-major)
+        bool transpose;
+    };
+    struct TaskBuild {
+        Task t;
+        std::vector<Seg> segs;
+        std::vector<Piece> pieces;
+    };
+    std::vector<std::vector<TaskBuild>> phases(4 + 2 * nl);
+    // index: 0 near, 1 upleaf, 2 leafexp, 3.. up[l] (3 + l), down[l] (3 + nl + l)
+    const int IDX_NEAR = 0, IDX_UPLEAF = 1, IDX_LEAFEXP = 2;
+    auto idx_up = [&](int l) { return 3 + l; };
+    auto idx_down = [&](int l) { return 3 + nl + l; };
+
+    auto new_task = [&](int32_t out_off, int32_t m) {
+        TaskBuild tb;
+        tb.t.out_off = out_off;
+        tb.t.m = m;
+        tb.t.mpad = m + (m & 1);
+        tb.t.ncol = 0;
+        tb.t.mat_off = 0;
+        return tb;
+    };
+    int64_t near_elems = 0, coupling_elems = 0, transfer_elems = 0, leaf_elems = 0, nleaves = 0;
+    int64_t near_blocks = 0, adm_blocks = 0;
+    int32_t max_rank = 0;
+    for (int t = 0; t < nc; ++t) max_rank = std::max(max_rank, rk[t]);
+
+    for (int t = 0; t < nc; ++t) {
+        const int32_t kt = rk[t];
+        const int l = level[t];
+        if (leaf(t)) {
+            ++nleaves;
+            // near field
+            TaskBuild tb = new_task(tree->begin[t], tree->size[t]);
+            for (int j = data->near_ptr[t]; j < data->near_ptr[t + 1]; ++j) {
+                const int s = data->near_col[j];
+                tb.segs.push_back({tree->begin[s], tree->size[s]});
+                tb.pieces.push_back({0, data->Z_off[j], tree->size[t], tree->size[s], false});
+                tb.t.ncol += tree->size[s];
+                near_elems += (int64_t)tree->size[t] * tree->size[s];
+                ++near_blocks;
+            }
+            if (tb.t.ncol > 0) phases[IDX_NEAR].push_back(std::move(tb));
+            if (kt > 0) {
+                leaf_elems += (int64_t)tree->size[t] * kt;
+                TaskBuild f = new_task((int32_t)h->xo[t], kt);
+                f.segs.push_back({tree->begin[t], tree->size[t]});
+                f.pieces.push_back({data->W ? 2 : 1, data->W ? data->W_off[t] : data->U_off[t],
+                                    tree->size[t], kt, true});
+                f.t.ncol = tree->size[t];
+                phases[IDX_UPLEAF].push_back(std::move(f));
+                TaskBuild b = new_task(tree->begin[t], tree->size[t]);
+                b.segs.push_back({enc1(ktot + h->xo[t]), kt});
+                b.pieces.push_back({1, data->U_off[t], tree->size[t], kt, false});
+                b.t.ncol = kt;
+                phases[IDX_LEAFEXP].push_back(std::move(b));
+            }
+        } else if (kt > 0) {
+            TaskBuild u = new_task((int32_t)h->xo[t], kt);
+            for (int c = 0; c < 2; ++c) {
+                const int ch = tree->child[2 * t + c];
+                if (rk[ch] == 0) continue;
+                u.segs.push_back({enc1(h->xo[ch]), rk[ch]});
+                u.pieces.push_back({3, data->T_off[ch], rk[ch], kt, true});
+                u.t.ncol += rk[ch];
+            }
+            if (u.t.ncol > 0) phases[idx_up(l)].push_back(std::move(u));
+        }
+        if (t > 0 && kt > 0 && rk[parent[t]] > 0) transfer_elems += (int64_t)kt * rk[parent[t]];
+        // coupling + downward transfer
+        if (kt > 0) {
+            TaskBuild d = new_task((int32_t)(ktot + h->xo[t]), kt);
+            for (int j = data->adm_ptr[t]; j < data->adm_ptr[t + 1]; ++j) {
+                const int s = data->adm_col[j];
+                ++adm_blocks;
+                if (rk[s] == 0) continue;
+                d.segs.push_back({enc1(h->xo[s]), rk[s]});
+                d.pieces.push_back({4, data->S_off[j], kt, rk[s], false});
+                d.t.ncol += rk[s];
+                coupling_elems += (int64_t)kt * rk[s];
+            }
+            if (t > 0 && rk[parent[t]] > 0) {
+                const int p = parent[t];
+                d.segs.push_back({enc1(ktot + h->xo[p]), rk[p]});
+                d.pieces.push_back({3, data->T_off[t], kt, rk[p], false});
+                d.t.ncol += rk[p];
+            }
+            if (d.t.ncol > 0) phases[idx_down(l)].push_back(std::move(d));
+        } else {
+            adm_blocks += data->adm_ptr[t + 1] - data->adm_ptr[t];
+        }
+    }
+
+    // ---- lay out matrices, sort tasks by decreasing work -------------------------------
+    int64_t mat_elems = 0;
+    int64_t nseg = 0, ntask = 0;
+    for (auto &ph : phases) {
+        std::stable_sort(ph.begin(), ph.end(), [](const TaskBuild &a, const TaskBuild &b) {
+            return (int64_t)a.t.mpad * a.t.ncol > (int64_t)b.t.mpad * b.t.ncol;
+        });
+        for (auto &tb : ph) {
+            tb.t.mat_off = mat_elems;
+            mat_elems += ((int64_t)tb.t.mpad * tb.t.ncol + 31) / 32 * 32;
+            tb.t.seg_begin = (int32_t)nseg;
+            nseg += (int64_t)tb.segs.size();
+            tb.t.seg_end = (int32_t)nseg;
+            ++ntask;
+        }
+    }
+    if (nseg > INT32_MAX) {
+        delete h;
+        return arg_error("too many blocks");
+    }
+    std::vector<float2> hmat;
+    try {
+        hmat.assign((size_t)std::max<int64_t>(mat_elems, 32), make_float2(0.f, 0.f));
+    } catch (...) {
+        delete h;
+        set_error("host allocation of the staging matrix failed");
+        return H2_ERR_ALLOC;
+    }
+    const CplxIn srcZ{data->Z, data->dtype}, srcU{data->U, data->dtype}, srcW{data->W, data->dtype},
+        srcT{data->T, data->dtype}, srcS{data->S, data->dtype};
+    bool finite = true;
+    for (auto &ph : phases) {
+        const int64_t np = (int64_t)ph.size();
+#pragma omp parallel for schedule(dynamic, 4) reduction(&& : finite)
+        for (int64_t i = 0; i < np; ++i) {
+            const TaskBuild &tb = ph[i];
+            float2 *dst = hmat.data() + tb.t.mat_off;
+            int64_t col = 0;
+            for (const Piece &pc : tb.pieces) {
+                const CplxIn &src = pc.kind == 0 ? srcZ : pc.kind == 1 ? srcU : pc.kind == 2 ? srcW
+                                                         : pc.kind == 3 ? srcT : srcS;
+                const int32_t orows = pc.transpose ? pc.cols : pc.rows;  // rows placed
+                const int32_t ocols = pc.transpose ? pc.rows : pc.cols;
+                for (int32_t j = 0; j < ocols; ++j) {
+                    float2 *dc = dst + (col + j) * tb.t.mpad;
+                    for (int32_t r = 0; r < orows; ++r) {
+                        const int64_t si = pc.transpose ? pc.off + (int64_t)r * pc.rows + j
+                                                        : pc.off + (int64_t)j * pc.rows + r;
+                        const float2 v = src.at(si);
+                        finite = finite && std::isfinite(v.x) && std::isfinite(v.y);
+                        dc[r] = v;
+                    }
+                }
+                col += ocols;
+            }
+        }
+    }
+    if (!finite) {
+        delete h;
+        return arg_error("data: non-finite entry (or entry overflowing FP32)");
+    }
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        delete h;
+        set_error("no CUDA device " + std::to_string(device));
+        return H2_ERR_CUDA;
+    }
+
+    // ---- upload ---------------------------------------------------------------------
+    std::vector<Task> htasks;
+    std::vector<Seg> hsegs;
+    htasks.reserve(ntask);
+    hsegs.reserve(nseg);
+    for (auto &ph : phases)
+        for (auto &tb : ph) {
+            htasks.push_back(tb.t);
+            hsegs.insert(hsegs.end(), tb.segs.begin(), tb.segs.end());
+        }
+    auto fail = [&](h2_status s) {
+        h2_free(h);
+        return s;
+    };
+    if (cudaSetDevice(device) != cudaSuccess) return fail(H2_ERR_CUDA);
+#define H2_LOAD_CUDA(call)                                                         \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) {                                                  \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));        \
+            return fail(e__ == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA); \
+        }                                                                          \
+    } while (0)
+    H2_LOAD_CUDA(cudaMalloc(&h->d_mat, hmat.size() * sizeof(float2)));
+    H2_LOAD_CUDA(cudaMemcpy(h->d_mat, hmat.data(), hmat.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    h->mat_elems = mat_elems;
+    hmat.clear();
+    hmat.shrink_to_fit();
+    H2_LOAD_CUDA(cudaMalloc(&h->d_segs, std::max<size_t>(1, hsegs.size()) * sizeof(Seg)));
+    if (!hsegs.empty())
+        H2_LOAD_CUDA(cudaMemcpy(h->d_segs, hsegs.data(), hsegs.size() * sizeof(Seg), cudaMemcpyHostToDevice));
+    H2_LOAD_CUDA(cudaMalloc(&h->d_tasks, std::max<size_t>(1, htasks.size()) * sizeof(Task)));
+    if (!htasks.empty())
+        H2_LOAD_CUDA(cudaMemcpy(h->d_tasks, htasks.data(), htasks.size() * sizeof(Task), cudaMemcpyHostToDevice));
+    H2_LOAD_CUDA(cudaMalloc(&h->d_coef, std::max<int64_t>(1, 2 * ktot) * sizeof(double2)));
+    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking));
+    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming));
+
+    // ---- phases ---------------------------------------------------------------------
+    int64_t tpos = 0;
+    auto fill = [&](Phase &P, const char *name, std::vector<TaskBuild> &src) {
+        P.name = name;
+        P.tasks.clear();
+        for (auto &tb : src) {
+            P.tasks.push_back(tb.t);
+            P.max_mpad = std::max(P.max_mpad, tb.t.mpad);
+            P.max_ncol = std::max(P.max_ncol, tb.t.ncol);
+            P.elems += (int64_t)tb.t.m * tb.t.ncol;
+        }
+        P.d_tasks = h->d_tasks + tpos;
+        tpos += (int64_t)src.size();
+        P.threads = choose_threads(P.tasks);
+    };
+    fill(h->near, "near", phases[IDX_NEAR]);
+    fill(h->upleaf, "upleaf", phases[IDX_UPLEAF]);
+    fill(h->leafexp, "leafexp", phases[IDX_LEAFEXP]);
+    h->up.resize(nl);
+    h->down.resize(nl);
+    for (int l = 0; l < nl; ++l) fill(h->up[l], "up", phases[idx_up(l)]);
+    for (int l = 0; l < nl; ++l) fill(h->down[l], "down", phases[idx_down(l)]);
+
+    h2_stats &S = h->stats;
+    S.n = n;
+    S.n_clusters = nc;
+    S.n_leaves = nleaves;
+    S.n_levels = nl;
+    S.near_blocks = near_blocks;
+    S.adm_blocks = adm_blocks;
+    S.near_elems = near_elems;
+    S.coupling_elems = coupling_elems;
+    S.transfer_elems = transfer_elems;
+    S.leaf_elems = leaf_elems;
+    S.max_rank = max_rank;
+    S.device_bytes = (int64_t)std::max<int64_t>(mat_elems, 32) * 8 + (int64_t)hsegs.size() * sizeof(Seg) +
+                     (int64_t)htasks.size() * sizeof(Task) + 2 * ktot * 16;
+    *out = h;
+    return H2_OK;
+}
+
+h2_status h2_get_stats(const h2_handle *h, h2_stats *out)
+{
+    if (!h || !out) return arg_error("NULL argument");
+    *out = h->stats;
+    return H2_OK;
+}
+
+}  // extern "C"
+
+// ---- products -------------------------------------------------------------------------
+
+template <typename VT>
+static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st)
+{
+    VT *coef = reinterpret_cast<VT *>(h->d_coef);
+    const float2 *mat = h->d_mat;
+    const Seg *segs = h->d_segs;
+    auto launch = [&](const Phase &ph, const VT *in0, VT *outp, int beta, cudaStream_t s) {
+        if constexpr (std::is_same<VT, float2>::value)
+            return launch_phase_f32(ph, mat, segs, in0, coef, outp, beta, s);
+        else
+            return launch_phase_f64(ph, mat, segs, in0, coef, outp, beta, s);
+    };
+    H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(VT) * 2 * std::max<int64_t>(1, h->ktot), st));
+    H2_CUDA(cudaEventRecord(h->ev_fork, st));
+    H2_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
+    H2_CUDA(launch(h->near, x, y, 0, h->s_aux));
+    H2_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
+    H2_CUDA(launch(h->upleaf, x, coef, 0, st));
+    for (int l = h->nlev - 1; l >= 0; --l) H2_CUDA(launch(h->up[l], x, coef, 0, st));
+    for (int l = 0; l < h->nlev; ++l) H2_CUDA(launch(h->down[l], x, coef, 0, st));
+    H2_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
+    H2_CUDA(launch(h->leafexp, x, y, 1, st));
+    return H2_OK;
+}
+
+extern "C" {
+
+h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t ld, h2_prec prec,
+                    void *stream)
+{
+    if (!h || !x || !y) return arg_error("h2_matvec: NULL argument");
+    if (nrhs < 1) return arg_error("h2_matvec: nrhs must be >= 1");
+    if (nrhs > 1 && ld < h->n) return arg_error("h2_matvec: ld < n");
+    if (x == y) return arg_error("h2_matvec: x and y must not overlap");
+    if (prec == H2_PREC_SPLITBF16) return arg_error("h2_matvec: split-bf16 path not available");
+    if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC) return arg_error("h2_matvec: bad precision");
+    H2_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int32_t r = 0; r < nrhs; ++r) {
+        h2_status s;
+        if (prec == H2_PREC_FP32)
+            s = run_single<float2>(h, reinterpret_cast<const float2 *>(x) + (int64_t)r * ld,
+                                   reinterpret_cast<float2 *>(y) + (int64_t)r * ld, st);
+        else
+            s = run_single<double2>(h, reinterpret_cast<const double2 *>(x) + (int64_t)r * ld,
+                                    reinterpret_cast<double2 *>(y) + (int64_t)r * ld, st);
+        if (s != H2_OK) return s;
+    }
+    return H2_OK;
+}
+
+h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host, int32_t nrhs, int64_t ld,
+                         h2_prec prec)
+{
+    if (!h || !x_host || !y_host) return arg_error("h2_matvec_host: NULL argument");
+    if (nrhs < 1) return arg_error("h2_matvec_host: nrhs must be >= 1");
+    if (nrhs == 1) ld = h->n;
+    if (ld < h->n) return arg_error("h2_matvec_host: ld < n");
+    const size_t esz = prec == H2_PREC_FP64ACC ? sizeof(double2) : sizeof(float2);
+    const int64_t bytes = (int64_t)esz * ld * nrhs;
+    H2_CUDA(cudaSetDevice(h->device));
+    if (bytes > h->buf_bytes) {
+        cudaFree(h->d_xbuf);
+        cudaFree(h->d_ybuf);
+        h->d_xbuf = h->d_ybuf = nullptr;
+        h->buf_bytes = 0;
+        if (cudaMalloc(&h->d_xbuf, bytes) != cudaSuccess || cudaMalloc(&h->d_ybuf, bytes) != cudaSuccess) {
+            set_error("h2_matvec_host: staging allocation failed");
+            return H2_ERR_ALLOC;
+        }
+        h->buf_bytes = bytes;
+    }
+    cudaStream_t st = nullptr;  // legacy default stream
+    H2_CUDA(cudaMemcpyAsync(h->d_xbuf, x_host, bytes, cudaMemcpyHostToDevice, st));
+    h2_status s = h2_matvec(h, h->d_xbuf, h->d_ybuf, nrhs, ld, prec, st);
+    if (s != H2_OK) return s;
+    H2_CUDA(cudaMemcpyAsync(y_host, h->d_ybuf, bytes, cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaStreamSynchronize(st));
+    return H2_OK;
+}
+
+h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters, double *ms, int32_t n_ms)
+{
+    if (!h || !x || !y || !ms || iters < 1 || n_ms < 1) return arg_error("h2_profile_matvec: bad argument");
+    H2_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->s_aux;
+    const float2 *xx = reinterpret_cast<const float2 *>(x);
+    float2 *yy = reinterpret_cast<float2 *>(y);
+    float2 *coef = reinterpret_cast<float2 *>(h->d_coef);
+    cudaEvent_t ev[6];
+    for (auto &e : ev) H2_CUDA(cudaEventCreate(&e));
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int it = 0; it <= iters; ++it) {
+        H2_CUDA(cudaEventRecord(ev[0], st));
+        H2_CUDA(launch_phase_f32(h->near, h->d_mat, h->d_segs, xx, coef, yy, 0, st));
+        H2_CUDA(cudaEventRecord(ev[1], st));
+        H2_CUDA(launch_phase_f32(h->upleaf, h->d_mat, h->d_segs, xx, coef, coef, 0, st));
+        H2_CUDA(cudaEventRecord(ev[2], st));
+        for (int l = h->nlev - 1; l >= 0; --l)
+            H2_CUDA(launch_phase_f32(h->up[l], h->d_mat, h->d_segs, xx, coef, coef, 0, st));
+        H2_CUDA(cudaEventRecord(ev[3], st));
+        for (int l = 0; l < h->nlev; ++l)
+            H2_CUDA(launch_phase_f32(h->down[l], h->d_mat, h->d_segs, xx, coef, coef, 0, st));
+        H2_CUDA(cudaEventRecord(ev[4], st));
+        H2_CUDA(launch_phase_f32(h->leafexp, h->d_mat, h->d_segs, xx, coef, yy, 1, st));
+        H2_CUDA(cudaEventRecord(ev[5], st));
+        H2_CUDA(cudaEventSynchronize(ev[5]));
+        if (it == 0) continue;  // warm-up
+        for (int k = 0; k < 5; ++k) {
+            float f = 0;
+            H2_CUDA(cudaEventElapsedTime(&f, ev[k], ev[k + 1]));
+            acc[k] += f;
+        }
+    }
+    // whole product on the concurrent path
+    H2_CUDA(cudaEventRecord(ev[0], st));
+    for (int it = 0; it < iters; ++it) {
+        h2_status s = run_single<float2>(h, xx, yy, st);
+        if (s != H2_OK) return s;
+    }
+    H2_CUDA(cudaEventRecord(ev[1], st));
+    H2_CUDA(cudaEventSynchronize(ev[1]));
+    float f = 0;
+    H2_CUDA(cudaEventElapsedTime(&f, ev[0], ev[1]));
+    acc[5] = f;
+    for (auto &e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < n_ms && k < 6; ++k) ms[k] = acc[k] / iters;
+    return H2_OK;
+}
+
+}  // extern "C"

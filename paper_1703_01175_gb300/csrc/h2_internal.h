@@ -1,0 +1,89 @@
+// Internal declarations of libh2 (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "h2.h"
+
+namespace h2 {
+
+// One output segment of a block-row product:
+//   out[out_off + i] (+)= sum_c M[i, c] * in(c),   i < m, c < ncol
+// M is the task's own column-major matrix of mpad x ncol complex entries
+// stored at mat[mat_off] (mpad = m rounded up to even, zero padded), and the
+// input column c is gathered from the task's segments (in order).
+struct Task {
+    int32_t out_off;
+    int32_t m;
+    int32_t mpad;
+    int32_t ncol;
+    int64_t mat_off;
+    int32_t seg_begin;
+    int32_t seg_end;
+};
+
+// A run of n consecutive input entries: in0[in_off ...] when in_off >= 0,
+// else in1[-in_off - 1 ...].
+struct Seg {
+    int32_t in_off;
+    int32_t n;
+};
+
+// A batch of independent tasks executed by one launch.
+struct Phase {
+    const char *name = "";
+    std::vector<Task> tasks;       // host copy, sorted by decreasing work
+    Task *d_tasks = nullptr;       // device copy (points into the handle's task pool)
+    int32_t max_mpad = 0;
+    int32_t max_ncol = 0;
+    int64_t elems = 0;             // matrix entries streamed (sum of m * ncol)
+    int threads = 256;
+    int ntask() const { return (int)tasks.size(); }
+};
+
+enum PhaseKind { PH_NEAR = 0, PH_UPLEAF, PH_UP, PH_DOWN, PH_LEAFEXP, PH_COUNT };
+
+void set_error(const std::string &msg);
+
+}  // namespace h2
+
+struct h2_handle {
+    int device = 0;
+    int32_t n = 0, nc = 0, nlev = 0;
+    std::vector<int32_t> level_ptr, child, begin, size, rank, parent, level;
+    std::vector<int32_t> xo;      // offset of xh^t in the coefficient buffer
+    int64_t ktot = 0;             // sum of ranks; yh^t lives at ktot + xo[t]
+
+    // device storage
+    float2 *d_mat = nullptr;      // all task matrices
+    int64_t mat_elems = 0;
+    h2::Seg *d_segs = nullptr;
+    h2::Task *d_tasks = nullptr;
+    void *d_coef = nullptr;       // 2 * ktot coefficients (sized for c128)
+    void *d_xbuf = nullptr;       // staging for the host-pointer entry point
+    void *d_ybuf = nullptr;
+    int64_t buf_bytes = 0;
+
+    h2::Phase near, upleaf, leafexp;
+    std::vector<h2::Phase> up;    // per level (index = level of the output cluster)
+    std::vector<h2::Phase> down;  // per level
+
+    cudaStream_t s_aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_near = nullptr;
+
+    h2_stats stats{};
+};
+
+namespace h2 {
+// launch one phase; VT = float2 (FP32) or double2 (FP64 accumulation)
+cudaError_t launch_phase_f32(const Phase &ph, const float2 *mat, const Seg *segs,
+                             const float2 *in0, const float2 *in1, float2 *out,
+                             int beta_one, cudaStream_t st);
+cudaError_t launch_phase_f64(const Phase &ph, const float2 *mat, const Seg *segs,
+                             const double2 *in0, const double2 *in1, double2 *out,
+                             int beta_one, cudaStream_t st);
+}  // namespace h2

@@ -1,0 +1,288 @@
+"""ctypes binding of libh2 (include/h2.h): argument marshalling only.
+
+Every step of the product and the solve runs in the CUDA library; this module
+only flattens block dictionaries into the C-ABI arrays, checks tensor dtypes and
+devices, and passes raw pointers. If the library is missing it raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libh2.so")
+
+H2_OK, H2_ERR_ARG, H2_ERR_ALLOC, H2_ERR_CUDA = 0, 1, 2, 3
+H2_ERR_NOT_CONVERGED, H2_ERR_BREAKDOWN, H2_ERR_TIMEOUT, H2_ERR_STATE = 4, 5, 6, 7
+H2_C64, H2_C128 = 0, 1
+PREC = {"fp32": 0, "splitbf16": 1, "fp64acc": 2}
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("n_clusters", ctypes.c_int32), ("n_levels", ctypes.c_int32),
+                ("level_ptr", _i32p), ("child", _i32p), ("begin", _i32p), ("size", _i32p),
+                ("rank", _i32p)]
+
+
+class _Data(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int),
+                ("U", ctypes.c_void_p), ("U_off", _i64p), ("U_len", ctypes.c_int64),
+                ("W", ctypes.c_void_p), ("W_off", _i64p), ("W_len", ctypes.c_int64),
+                ("T", ctypes.c_void_p), ("T_off", _i64p), ("T_len", ctypes.c_int64),
+                ("adm_ptr", _i32p), ("adm_col", _i32p),
+                ("S", ctypes.c_void_p), ("S_off", _i64p), ("S_len", ctypes.c_int64),
+                ("near_ptr", _i32p), ("near_col", _i32p),
+                ("Z", ctypes.c_void_p), ("Z_off", _i64p), ("Z_len", ctypes.c_int64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "n", "n_clusters", "n_leaves", "n_levels", "near_blocks", "adm_blocks", "near_elems",
+        "coupling_elems", "transfer_elems", "leaf_elems", "device_bytes")] + [("max_rank", ctypes.c_int32)]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libh2 (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1703_01175_gb300.build.build_all()")
+    L = ctypes.CDLL(LIB_PATH)
+    L.h2_load.restype = ctypes.c_int
+    L.h2_load.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Data), ctypes.c_char_p,
+                          ctypes.POINTER(ctypes.c_void_p)]
+    L.h2_free.restype = None
+    L.h2_free.argtypes = [ctypes.c_void_p]
+    L.h2_matvec.restype = ctypes.c_int
+    L.h2_matvec.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                            ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    L.h2_matvec_host.restype = ctypes.c_int
+    L.h2_matvec_host.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                 ctypes.c_int64, ctypes.c_int]
+    L.h2_get_stats.restype = ctypes.c_int
+    L.h2_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Stats)]
+    L.h2_profile_matvec.restype = ctypes.c_int
+    L.h2_profile_matvec.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
+    L.h2_status_string.restype = ctypes.c_char_p
+    L.h2_status_string.argtypes = [ctypes.c_int]
+    L.h2_last_error.restype = ctypes.c_char_p
+    L.h2_last_error.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != H2_OK:
+        L = lib()
+        raise H2Error(status, where, f"{L.h2_status_string(status).decode()}: {L.h2_last_error().decode()}")
+
+
+def exported_symbols() -> list:
+    """Names declared in include/h2.h (the C ABI)."""
+    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
+            "h2_profile_matvec", "h2_status_string", "h2_last_error"]
+
+
+# ---------------------------------------------------------------------------
+# Flat arrays of an H^2 representation (the h2_tree / h2_data layout).
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class H2Arrays:
+    n: int
+    level_ptr: np.ndarray   # int32 [n_levels + 1]
+    child: np.ndarray       # int32 [2 * nc]
+    begin: np.ndarray       # int32 [nc]
+    size: np.ndarray        # int32 [nc]
+    rank: np.ndarray        # int32 [nc]
+    U: np.ndarray           # complex, flat
+    U_off: np.ndarray       # int64 [nc]
+    W: np.ndarray | None
+    W_off: np.ndarray | None
+    T: np.ndarray
+    T_off: np.ndarray
+    adm_ptr: np.ndarray
+    adm_col: np.ndarray
+    S: np.ndarray
+    S_off: np.ndarray
+    near_ptr: np.ndarray
+    near_col: np.ndarray
+    Z: np.ndarray
+    Z_off: np.ndarray
+
+    @property
+    def nc(self) -> int:
+        return int(self.size.shape[0])
+
+
+def _flatten(blocks: dict, keys, nc_or_len: int, dtype):
+    """Concatenate column-major blocks; returns (flat, offsets)."""
+    off = np.zeros(nc_or_len, dtype=np.int64)
+    parts = []
+    pos = 0
+    for i, key in enumerate(keys):
+        if key is None or key not in blocks:
+            continue
+        b = np.asarray(blocks[key])
+        off[i] = pos
+        parts.append(np.asfortranarray(b).reshape(-1, order="F").astype(dtype, copy=False))
+        pos += b.size
+    flat = np.concatenate(parts) if parts else np.zeros(1, dtype=dtype)
+    return np.ascontiguousarray(flat), off
+
+
+def arrays_from_blocks(n, level_ptr, child, begin, size, rank, U: dict, W: dict | None,
+                       T: dict, S: dict, Z: dict, dtype=np.complex128) -> H2Arrays:
+    """Marshal per-block dictionaries (cluster -> matrix, (t, s) -> matrix) into
+    the flat CSR arrays of h2_data. Blocks are column-major in the output."""
+    nc = len(size)
+    child = np.asarray(child, dtype=np.int32).reshape(-1)
+    Uf, Uo = _flatten(U, range(nc), nc, dtype)
+    if W is not None:
+        Wf, Wo = _flatten(W, range(nc), nc, dtype)
+    else:
+        Wf, Wo = None, None
+    Tf, To = _flatten(T, range(nc), nc, dtype)
+    adm = sorted(S.keys())
+    near = sorted(Z.keys())
+    adm_ptr = np.zeros(nc + 1, dtype=np.int32)
+    for t, _ in adm:
+        adm_ptr[t + 1] += 1
+    adm_ptr = np.cumsum(adm_ptr).astype(np.int32)
+    near_ptr = np.zeros(nc + 1, dtype=np.int32)
+    for t, _ in near:
+        near_ptr[t + 1] += 1
+    near_ptr = np.cumsum(near_ptr).astype(np.int32)
+    Sf, So = _flatten(S, adm, len(adm), dtype)
+    Zf, Zo = _flatten(Z, near, len(near), dtype)
+    return H2Arrays(int(n), np.asarray(level_ptr, dtype=np.int32), child,
+                    np.asarray(begin, dtype=np.int32), np.asarray(size, dtype=np.int32),
+                    np.asarray(rank, dtype=np.int32), Uf, Uo, Wf, Wo, Tf, To,
+                    adm_ptr, np.array([s for _, s in adm] or [0], dtype=np.int32), Sf, So,
+                    near_ptr, np.array([s for _, s in near] or [0], dtype=np.int32), Zf, Zo)
+
+
+def _ip(a, t):
+    return a.ctypes.data_as(t) if a is not None else None
+
+
+class H2Matrix:
+    """A loaded H^2 operator on one GPU (wraps an h2_handle)."""
+
+    def __init__(self, arrs: H2Arrays, device: int = 0):
+        L = lib()
+        cplx = arrs.U.dtype
+        if cplx not in (np.complex64, np.complex128):
+            raise TypeError("block arrays must be complex64 or complex128")
+        for name in ("W", "T", "S", "Z"):
+            a = getattr(arrs, name)
+            if a is not None and a.dtype != cplx:
+                raise TypeError(f"{name} has dtype {a.dtype}, expected {cplx}")
+        self._keep = arrs
+        self.n = arrs.n
+        tr = _Tree(arrs.n, arrs.nc, len(arrs.level_ptr) - 1, _ip(arrs.level_ptr, _i32p),
+                   _ip(arrs.child, _i32p), _ip(arrs.begin, _i32p), _ip(arrs.size, _i32p),
+                   _ip(arrs.rank, _i32p))
+        dt = H2_C64 if cplx == np.complex64 else H2_C128
+        d = _Data(dt,
+                  arrs.U.ctypes.data, _ip(arrs.U_off, _i64p), arrs.U.size,
+                  arrs.W.ctypes.data if arrs.W is not None else None, _ip(arrs.W_off, _i64p),
+                  arrs.W.size if arrs.W is not None else 0,
+                  arrs.T.ctypes.data, _ip(arrs.T_off, _i64p), arrs.T.size,
+                  _ip(arrs.adm_ptr, _i32p), _ip(arrs.adm_col, _i32p),
+                  arrs.S.ctypes.data, _ip(arrs.S_off, _i64p), arrs.S.size,
+                  _ip(arrs.near_ptr, _i32p), _ip(arrs.near_col, _i32p),
+                  arrs.Z.ctypes.data, _ip(arrs.Z_off, _i64p), arrs.Z.size)
+        h = ctypes.c_void_p()
+        _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), f"device={device}".encode(),
+                         ctypes.byref(h)), "h2_load")
+        self._h = h
+        self.device = device
+        self._keep = None  # the library copied everything
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().h2_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib().h2_get_stats(self._h, ctypes.byref(s)), "h2_get_stats")
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def matvec(self, x, y=None, prec: str = "fp32", stream=None):
+        """y = A x on the device. x: torch complex64 (fp32, splitbf16) or
+        complex128 (fp64acc) CUDA tensor of shape (n,) or (n, nrhs) column-major
+        (i.e. x.t() contiguous) or (nrhs, n) contiguous rows via x.T."""
+        import torch
+        want = torch.complex128 if prec == "fp64acc" else torch.complex64
+        if x.dtype != want or not x.is_cuda:
+            raise TypeError(f"x must be a CUDA {want} tensor")
+        nrhs, ld = self._shape(x)
+        if y is None:
+            y = torch.empty_like(x)
+        if y.dtype != want or y.shape != x.shape or not y.is_cuda:
+            raise TypeError("y must match x")
+        self._shape(y)
+        st = torch.cuda.current_stream(x.device).cuda_stream if stream is None else stream
+        _check(lib().h2_matvec(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                               nrhs, ld, PREC[prec], ctypes.c_void_p(st)), "h2_matvec")
+        return y
+
+    def _shape(self, x):
+        if x.dim() == 1:
+            if x.shape[0] != self.n or x.stride(0) != 1:
+                raise ValueError("vector length or stride mismatch")
+            return 1, self.n
+        if x.dim() == 2 and x.shape[0] == self.n and x.stride(0) == 1:
+            return x.shape[1], x.stride(1) if x.shape[1] > 1 else self.n
+        raise ValueError("x must be (n,) or (n, nrhs) with unit stride along n")
+
+    def matvec_host(self, x: np.ndarray, prec: str = "fp32") -> np.ndarray:
+        """y = A x with host numpy arrays (copies inside the call)."""
+        want = np.complex128 if prec == "fp64acc" else np.complex64
+        x = np.asarray(x)
+        if x.dtype != want:
+            raise TypeError(f"x must be {want}")
+        nrhs = 1 if x.ndim == 1 else x.shape[1]
+        xf = np.asfortranarray(x)
+        y = np.empty_like(xf, order="F")
+        _check(lib().h2_matvec_host(self._h, xf.ctypes.data, y.ctypes.data, nrhs, self.n, PREC[prec]),
+               "h2_matvec_host")
+        return y
+
+    def profile(self, x, y, iters: int = 10) -> dict:
+        ms = (ctypes.c_double * 6)()
+        _check(lib().h2_profile_matvec(self._h, ctypes.c_void_p(x.data_ptr()),
+                                       ctypes.c_void_p(y.data_ptr()), iters, ms, 6),
+               "h2_profile_matvec")
+        keys = ["near", "leaf_forward", "upward", "coupling_downward", "leaf_expansion", "total"]
+        return dict(zip(keys, list(ms)))

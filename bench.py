@@ -1,0 +1,326 @@
+"""Benchmark of the GB300 H^2 VIE product and solve.
+
+Workload (default): the 32^3-voxel dielectric cube (side 2 wavelengths,
+eps_r ~ U[2,6] per voxel, N = 98,304 unknowns, leaf 96, eta = 1, eps = 1e-4),
+single right-hand side, FP32 product. One step = one H^2 matrix-vector product
+(leaf forward, upward transfers, couplings, downward transfers, leaf
+expansion, near field) with the H^2 data resident in HBM; the data is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the product
+does not shard across GPUs here) and rank 0 prints the max over ranks.
+--impl reference times the FP64 CPU oracle on the same H^2 data on the host
+cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cube32"
+WORKLOAD_DESC = ("cube32: 32^3 voxel dielectric cube, side 2 lambda, eps_r ~ U[2,6] (seed 2), "
+                 "N=98304, leaf 96 unknowns, eta=1, eps=1e-4, 1 RHS")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(name: str):
+    """H^2 arrays of the workload from the host constructor (setup, cached on
+    disk between runs). Returns (workload, arrays, tree permutation, seconds)."""
+    import synth
+    from paper_1703_01175_gb300 import construct
+    w = synth.workload(name)
+    v = w.voxels
+    t0 = time.time()
+    arrs, perm = construct.build_vie_h2_cached(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
+    return w, arrs, perm, time.time() - t0
+
+
+def _traffic_from_profile(kernel_src: str):
+    """Per-launch DRAM traffic of the near-field launch from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "rowgemv_near_cube32.txt")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != sha:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def oracle_matvec_fn(arrs, perm):
+    """The oracle's FP64 H^2 product on the given H^2 data (host cores)."""
+    from oracle import h2io, h2mv
+    h = h2io.from_flat(arrs, perm)
+    return lambda x: h2mv.h2_matvec(h, x)
+
+
+def _blas_threads():
+    try:
+        from paper_1703_01175_gb300.construct import _BlasThreads
+        fs, fg = _BlasThreads._lookup()
+        return fg() if fg is not None else os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w, arrs, perm, tb = build_workload(args.workload)
+    apply_h2 = oracle_matvec_fn(arrs, perm)
+    import synth
+    x = synth.random_complex(arrs.n, 1)
+    for _ in range(args.warmup):
+        apply_h2(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        apply_h2(x)
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    cores = _blas_threads()
+    line = {"impl": "reference", "metric": "h2_matvec_ms", "value": ms, "unit": "ms",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (fp64)",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": "one full FP64 H^2 product of the workload per step"},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1703_01175_gb300 import build, h2 as h2py
+    import synth
+
+    build.build_all()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w, arrs, perm, t_build = build_workload(args.workload)
+    A = h2py.H2Matrix(arrs, device=local_rank)
+    st = A.stats()
+    n = arrs.n
+    x_np = synth.random_complex(n, 1).astype(np.complex64)
+    x = torch.from_numpy(x_np).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        A.matvec(x, y)
+    torch.cuda.synchronize(dev)
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            A.matvec(x, y)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    if args.only_matvec:
+        A.close()
+        if rank == 0:
+            print(json.dumps({"metric": "h2_matvec_ms", "value": ms, "unit": "ms", "workload": args.workload,
+                              "steps": args.steps, "only_matvec": True}), flush=True)
+        return
+
+    # per-stage times on the launching stream (sequential, isolated)
+    prof = A.profile(x, y, iters=max(5, args.steps))
+    hbm, peak_kind = _peaks()
+    near_bytes = 8.0 * st["near_elems"] + 16.0 * n
+    near_gbs = near_bytes / (prof["near"] * 1e-3) / 1e9
+    total_bytes = 8.0 * (st["near_elems"] + st["coupling_elems"] + 2 * st["transfer_elems"]
+                         + 2 * st["leaf_elems"]) + 16.0 * n
+    mv_gbs = total_bytes / (ms * 1e-3) / 1e9
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_1703_01175_gb300", "csrc", "h2_gemv.cu"))
+
+    # GMRES to 1e-4: plain (FP32 products, FP64 Arnoldi) and with FP64-accumulated restart residuals
+    b_np = synth.default_rhs(w)[3 * perm[:, None] + np.arange(3)[None, :]].reshape(-1)
+    b = torch.from_numpy(b_np).to(dev)
+    gm = {"tol": w.tol, "restart": 50, "rhs": "x-polarised plane wave, +z incidence"}
+    for label, refine in (("plain", False), ("refined", True)):
+        A.gmres(b, tol=w.tol, restart=50, maxit=2000, refine=refine)  # warm-up (workspace)
+        torch.cuda.synchronize(dev)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        xs, info = A.gmres(b, tol=w.tol, restart=50, maxit=2000, refine=refine)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        gm[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
+                     "rel_res": info[0]["rel_res"], "status": info[0]["status"]}
+
+    # end to end through the host-pointer entry point
+    for _ in range(2):
+        A.matvec_host(x_np)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        A.matvec_host(x_np)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        apply_h2 = oracle_matvec_fn(arrs, perm)
+        xc = x_np.astype(np.complex128)
+        apply_h2(xc)
+        t0 = time.perf_counter()
+        reps = 0
+        while reps < 1 or (time.perf_counter() - t0 < 10.0 and reps < 3):
+            apply_h2(xc)
+            reps += 1
+        cpu_ms = (time.perf_counter() - t0) * 1e3 / reps
+        cpu = {"value": cpu_ms, "unit": "ms", "cores": _blas_threads(), "kind": "oracle",
+               "sample": f"{reps} full FP64 H^2 product(s) of the workload on the host (numpy)"}
+
+    A.close()
+    if rank != 0:
+        return
+    launches = st["kernels_per_matvec"]
+    line = {
+        "metric": "h2_matvec_ms", "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload, "l2": "H^2 data per step larger than L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}", "h2_build_s": round(t_build, 1),
+                   "h2_bytes_per_step": total_bytes, "near_blocks": st["near_blocks"],
+                   "adm_blocks": st["adm_blocks"], "max_rank": st["max_rank"]},
+        "matvec_gbs": mv_gbs, "matvec_frac_hbm": mv_gbs / hbm,
+        "stages_ms": prof,
+        "gmres": gm,
+        "roofline": {"bound": "hbm", "kernel": "rowgemv (near-field launch)", "achieved": near_gbs,
+                     "peak": hbm, "unit": "GB/s", "frac": near_gbs / hbm, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": near_bytes, "peak_source": peak_kind},
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")
+    ap.add_argument("--only-matvec", action="store_true",
+                    help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+        dist.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

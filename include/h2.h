@@ -142,6 +142,7 @@ typedef struct {
     int64_t leaf_elems;      /* sum of n_t k_t over leaves */
     int64_t device_bytes;    /* device memory held by the handle */
     int32_t max_rank;
+    int32_t kernels_per_matvec; /* libh2 kernel launches of one single-RHS FP32 product */
 } h2_stats;
 
 h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
@@ -156,6 +157,43 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
  */
 h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
                             double *ms, int32_t n_ms);
+
+/* Options of h2_gmres. */
+typedef struct {
+    double tol;        /* stop when ||b - A x||_2 <= tol ||b||_2 (true residual) */
+    int32_t restart;   /* Krylov subspace size m per cycle, 1..1024 */
+    int32_t maxit;     /* maximum total number of Arnoldi steps */
+    int32_t refine;    /* 1: restart residuals use the FP64-accumulated product
+                          (iterative refinement of the FP32 inner cycles) */
+    int32_t x0_given;  /* 1: x holds the initial guess on entry; 0: start from 0 */
+    int32_t precond;   /* 0: none; 1: learned preconditioner (flexible GMRES) */
+} h2_solve_opts;
+
+/* Per right-hand-side outcome of h2_gmres. */
+typedef struct {
+    int32_t iterations; /* Arnoldi steps taken */
+    int32_t restarts;   /* completed cycles */
+    double rel_res;     /* final true relative residual ||b - A x|| / ||b|| */
+    int32_t status;     /* H2_OK, H2_ERR_NOT_CONVERGED or H2_ERR_BREAKDOWN */
+} h2_solve_info;
+
+/*
+ * Solve A x = b by restarted GMRES(m) (Saad & Schultz) around the H^2
+ * product: Arnoldi with classical Gram-Schmidt applied twice in FP64 on c128
+ * vectors, Givens rotations and the Hessenberg least-squares solve on the
+ * device, FP32 H^2 products inside the cycles. Each restart recomputes the
+ * true residual (FP64-accumulated product when opts->refine). The paper's own
+ * solver is BiCGStab (Sec. V); this is the Krylov method around the same
+ * product (Sec. IV.B).
+ * b, x: device c128 arrays of nrhs columns (leading dimension ld >= N);
+ * right-hand sides are solved one after another. info: host array of nrhs
+ * entries (may be NULL). Returns H2_OK when every right-hand side converged,
+ * else the first failing status. Synchronises `stream` (convergence is read
+ * back once per Arnoldi step). Device workspace (N x (m+1) c128 basis) is
+ * allocated on first use and kept by the handle.
+ */
+h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld,
+                   const h2_solve_opts *opts, h2_solve_info *info, void *stream);
 
 const char *h2_status_string(h2_status s);
 

@@ -20,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIBH2 = os.path.join(HERE, "libh2.so")
+CSRC_HOST = os.path.join(HERE, "csrc_host")
+LIBH2BUILD = os.path.join(HERE, "libh2build.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
@@ -74,8 +76,31 @@ def build_libh2(verbose: bool = False, force: bool = False) -> str:
     return LIBH2
 
 
+def build_libh2build(verbose: bool = False, force: bool = False) -> str:
+    """Host-only constructor helpers (plain C++, portable: no -march flags)."""
+    srcs = sorted(glob.glob(os.path.join(CSRC_HOST, "*.cpp")))
+    hdrs = [os.path.join(INCLUDE, "h2build.h")]
+    if not force and not _stale(LIBH2BUILD, srcs + hdrs + [__file__]):
+        return LIBH2BUILD
+    cxx = os.environ.get("CXX") or shutil.which("g++") or "c++"
+    tmp = LIBH2BUILD + ".tmp"
+    cmd = [cxx, "-O3", "-std=c++17", "-fcx-limited-range", "-fPIC", "-shared", "-I" + INCLUDE, *srcs, "-o", tmp]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("g++ failed:\n" + r.stdout.decode(errors="replace"))
+    os.replace(tmp, LIBH2BUILD)
+    return LIBH2BUILD
+
+
 def build_all(verbose: bool = False, force: bool = False) -> None:
-    build_libh2(verbose=verbose, force=force)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(2) as ex:
+        a = ex.submit(build_libh2, verbose, force)
+        b = ex.submit(build_libh2build, verbose, force)
+        a.result()
+        b.result()
 
 
 if __name__ == "__main__":

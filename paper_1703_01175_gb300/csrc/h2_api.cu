@@ -231,6 +231,7 @@ void h2_free(h2_handle *h)
     cudaSetDevice(h->device);
     if (h->s_aux) cudaStreamSynchronize(h->s_aux);
     cudaDeviceSynchronize();
+    h2_free_krylov(h);
     cudaFree(h->d_mat);
     cudaFree(h->d_segs);
     cudaFree(h->d_tasks);
@@ -529,6 +530,14 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     S.transfer_elems = transfer_elems;
     S.leaf_elems = leaf_elems;
     S.max_rank = max_rank;
+    {
+        int nk = 0;
+        nk += h->near.ntask() > 0;
+        nk += h->upleaf.ntask() > 0;
+        nk += h->leafexp.ntask() > 0;
+        for (int l = 0; l < nl; ++l) nk += (h->up[l].ntask() > 0) + (h->down[l].ntask() > 0);
+        S.kernels_per_matvec = nk;
+    }
     S.device_bytes = (int64_t)std::max<int64_t>(mat_elems, 32) * 8 + (int64_t)hsegs.size() * sizeof(Seg) +
                      (int64_t)htasks.size() * sizeof(Task) + 2 * ktot * 16;
     *out = h;

@@ -76,7 +76,11 @@ struct h2_handle {
     cudaEvent_t ev_fork = nullptr, ev_near = nullptr;
 
     h2_stats stats{};
+
+    void *krylov = nullptr;       // GMRES workspace (h2_krylov.cu)
 };
+
+void h2_free_krylov(h2_handle *h);
 
 namespace h2 {
 // launch one phase; VT = float2 (FP32) or double2 (FP64 accumulation)

@@ -45,7 +45,18 @@ class _Data(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "n", "n_clusters", "n_leaves", "n_levels", "near_blocks", "adm_blocks", "near_elems",
-        "coupling_elems", "transfer_elems", "leaf_elems", "device_bytes")] + [("max_rank", ctypes.c_int32)]
+        "coupling_elems", "transfer_elems", "leaf_elems", "device_bytes")] + [
+        ("max_rank", ctypes.c_int32), ("kernels_per_matvec", ctypes.c_int32)]
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("precond", ctypes.c_int32)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("rel_res", ctypes.c_double),
+                ("status", ctypes.c_int32)]
 
 
 class H2Error(RuntimeError):
@@ -81,6 +92,9 @@ def lib() -> ctypes.CDLL:
     L.h2_profile_matvec.restype = ctypes.c_int
     L.h2_profile_matvec.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
+    L.h2_gmres.restype = ctypes.c_int
+    L.h2_gmres.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                           ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
     L.h2_status_string.restype = ctypes.c_char_p
     L.h2_status_string.argtypes = [ctypes.c_int]
     L.h2_last_error.restype = ctypes.c_char_p
@@ -98,7 +112,7 @@ def _check(status: int, where: str):
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
     return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
-            "h2_profile_matvec", "h2_status_string", "h2_last_error"]
+            "h2_profile_matvec", "h2_gmres", "h2_status_string", "h2_last_error"]
 
 
 # ---------------------------------------------------------------------------
@@ -278,6 +292,27 @@ class H2Matrix:
         _check(lib().h2_matvec_host(self._h, xf.ctypes.data, y.ctypes.data, nrhs, self.n, PREC[prec]),
                "h2_matvec_host")
         return y
+
+    def gmres(self, b, x=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
+              precond=0, stream=None, check=True):
+        """Solve A x = b on the device. b: CUDA complex128 (n,) or (n, nrhs)
+        column-major. Returns (x, [info dict per RHS])."""
+        import torch
+        if b.dtype != torch.complex128 or not b.is_cuda:
+            raise TypeError("b must be a CUDA complex128 tensor")
+        nrhs, ld = self._shape(b)
+        if x is None:
+            x = torch.zeros_like(b)
+        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), int(precond))
+        infos = (_SolveInfo * nrhs)()
+        st = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
+        status = lib().h2_gmres(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ld,
+                                ctypes.byref(opts), infos, ctypes.c_void_p(st))
+        out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status}
+               for i in infos]
+        if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
+            _check(status, "h2_gmres")
+        return x, out
 
     def profile(self, x, y, iters: int = 10) -> dict:
         ms = (ctypes.c_double * 6)()

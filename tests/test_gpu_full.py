@@ -1,0 +1,62 @@
+"""Full-size checks on the 32^3-voxel cube (N = 98,304, leaf 96, eps 1e-4):
+the H^2 data of the host constructor, the launch configuration bench.py times.
+
+- FP32 product vs the oracle's FP64 H^2 product on the same data: 1e-5;
+- sampled rows against the oracle's dense VIE rows, evaluated one by one:
+  representation error within 10 eps;
+- GMRES(50) to 1e-4: the oracle's FP64 residual of the GPU solution <= 1.05e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import h2io, h2mv, vie
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def full():
+    from paper_1703_01175_gb300 import build, construct, h2
+    build.build_all()
+    w = synth.workload("cube32")
+    v = w.voxels
+    arrs, perm = construct.build_vie_h2_cached(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
+    A = h2.H2Matrix(arrs)
+    hZ = h2io.from_flat(arrs, perm)
+    yield w, arrs, perm, A, hZ
+    A.close()
+
+
+def test_full_size_product_matches_oracle(full):
+    w, arrs, perm, A, hZ = full
+    x = synth.random_complex(arrs.n, 21)
+    y = A.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    y_or = h2mv.h2_matvec(hZ, x)
+    assert np.linalg.norm(y - y_or) <= 1e-5 * np.linalg.norm(y_or)
+    assert np.abs(y - y_or).max() <= 1e-5 * np.abs(y_or).max()
+    # sampled rows of the dense operator Z = I - K diag(chi), natural order
+    v = w.voxels
+    rng = np.random.default_rng(5)
+    rows_tree = np.sort(rng.choice(arrs.n, 24, replace=False))
+    unk = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)   # tree -> natural unknown
+    x_nat = np.empty_like(x)
+    x_nat[unk] = x
+    Zr = vie.z_rows(v.centres, v.dv, v.eps_r, 2 * math.pi, unk[rows_tree])
+    exact = Zr @ x_nat
+    err = np.abs(y[rows_tree] - exact)
+    assert err.max() <= 10 * w.eps * np.abs(exact).max()
+    assert np.linalg.norm(y[rows_tree] - exact) <= 10 * w.eps * np.linalg.norm(exact)
+
+
+def test_full_size_gmres_residual(full):
+    w, arrs, perm, A, hZ = full
+    b = synth.default_rhs(w)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
+    x, info = A.gmres(torch.from_numpy(b).cuda(), tol=w.tol, restart=50, maxit=2000, refine=True)
+    assert info[0]["status"] == 0, info
+    x = x.cpu().numpy()
+    res = np.linalg.norm(b - h2mv.h2_matvec(hZ, x)) / np.linalg.norm(b)
+    assert res <= 1.05 * w.tol

@@ -1,0 +1,83 @@
+"""GPU restarted GMRES against the oracle.
+
+Bar: the oracle's FP64 H^2 residual ||b - A x_gpu|| / ||b|| is at most the
+requested tolerance (times 1.05 for the plain FP32 restart residual), the GPU
+solution agrees with the oracle's GMRES solution to the accuracy the residual
+allows, and the outcome codes for non-convergence, zero right-hand sides and
+initial guesses are right.
+"""
+import numpy as np
+import pytest
+
+import cases
+import synth
+from oracle import krylov
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mats():
+    from paper_1703_01175_gb300 import build, h2
+    build.build_all()
+    out = {}
+    for name in ("cube8", "cube12", "ragged"):
+        out[name] = h2.H2Matrix(cases.get(name).arrays())
+    yield out
+    for m in out.values():
+        m.close()
+
+
+def _oracle_res(c, x, b):
+    return np.linalg.norm(b - c.oracle_matvec(x)) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("refine", [True, False])
+def test_gmres_cube8_matches_oracle(mats, refine):
+    c = cases.get("cube8")
+    w = synth.workload("cube8")
+    b = synth.default_rhs(w)[c.tree.unknown_perm()]
+    tol = 1e-6 if refine else 1e-5
+    xg, info = mats["cube8"].gmres(torch.from_numpy(b).cuda(), tol=tol, restart=50, refine=refine)
+    xg = xg.cpu().numpy()
+    assert info[0]["status"] == 0, info
+    res = _oracle_res(c, xg, b)
+    assert res <= tol * (1.0 if refine else 1.05) + 2e-7
+    xo, it, hist = krylov.gmres(c.oracle_matvec, b, tol, restart=50)
+    assert np.linalg.norm(xg - xo) <= 50 * tol * np.linalg.norm(xo)
+    assert abs(info[0]["iterations"] - it) <= 3
+
+
+def test_gmres_restart_and_multi_rhs(mats):
+    c = cases.get("cube12")
+    B = np.asfortranarray(synth.random_complex(c.n, 7, cols=2))
+    Bt = torch.from_numpy(B).cuda().t().contiguous().t()
+    X, info = mats["cube12"].gmres(Bt, tol=1e-4, restart=8, maxit=2000, refine=True)
+    X = X.cpu().numpy()
+    for j in range(2):
+        assert info[j]["status"] == 0
+        assert info[j]["restarts"] >= 2
+        assert _oracle_res(c, X[:, j], B[:, j]) <= 1e-4
+
+
+def test_gmres_not_converged_and_zero_rhs(mats):
+    c = cases.get("ragged")
+    b = synth.random_complex(c.n, 3)
+    x, info = mats["ragged"].gmres(torch.from_numpy(b).cuda(), tol=1e-12, restart=4, maxit=6)
+    assert info[0]["status"] == 4 and info[0]["iterations"] == 6  # H2_ERR_NOT_CONVERGED
+    assert info[0]["rel_res"] < 1.0
+    z = torch.zeros(c.n, dtype=torch.complex128, device="cuda")
+    x, info = mats["ragged"].gmres(z, tol=1e-6)
+    assert info[0]["status"] == 0 and torch.count_nonzero(x).item() == 0
+
+
+def test_gmres_initial_guess(mats):
+    c = cases.get("ragged")
+    b = synth.random_complex(c.n, 4)
+    bt = torch.from_numpy(b).cuda()
+    x, info = mats["ragged"].gmres(bt, tol=1e-8, restart=30, refine=True)
+    assert info[0]["status"] == 0
+    x2, info2 = mats["ragged"].gmres(bt, x=x.clone(), tol=1e-6, restart=30, refine=True, x0_given=True)
+    assert info2[0]["iterations"] == 0 and info2[0]["status"] == 0
+    assert torch.allclose(x, x2)

@@ -152,8 +152,8 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
  * the stream each stage is launched on. x, y: device c64 vectors. Runs `iters`
  * products (after one warm-up) and writes the mean duration in milliseconds
  * of each stage to ms[0..n_ms) in the order: near field, leaf forward,
- * upward transfers, coupling + downward transfers, leaf expansion, whole
- * product. Synchronous.
+ * upward transfers, couplings (all levels), downward transfers, leaf
+ * expansion, whole product (stages on the concurrent path). Synchronous.
  */
 h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
                             double *ms, int32_t n_ms);

@@ -302,10 +302,11 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         std::vector<Piece> pieces;
     };
     std::vector<std::vector<TaskBuild>> phases(4 + 2 * nl);
-    // index: 0 near, 1 upleaf, 2 leafexp, 3.. up[l] (3 + l), down[l] (3 + nl + l)
-    const int IDX_NEAR = 0, IDX_UPLEAF = 1, IDX_LEAFEXP = 2;
-    auto idx_up = [&](int l) { return 3 + l; };
-    auto idx_down = [&](int l) { return 3 + nl + l; };
+    // index: 0 near, 1 upleaf, 2 leafexp, 3 couple (all levels), 4.. up[l], down[l]
+    const int IDX_NEAR = 0, IDX_UPLEAF = 1, IDX_LEAFEXP = 2, IDX_COUPLE = 3;
+    auto idx_up = [&](int l) { return 4 + l; };
+    auto idx_down = [&](int l) { return 4 + nl + l; };
+    phases.resize(4 + 2 * nl);
 
     auto new_task = [&](int32_t out_off, int32_t m) {
         TaskBuild tb;
@@ -363,7 +364,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
             if (u.t.ncol > 0) phases[idx_up(l)].push_back(std::move(u));
         }
         if (t > 0 && kt > 0 && rk[parent[t]] > 0) transfer_elems += (int64_t)kt * rk[parent[t]];
-        // coupling + downward transfer
+        // couplings (all levels in one phase) and the downward transfer (per level)
         if (kt > 0) {
             TaskBuild d = new_task((int32_t)(ktot + h->xo[t]), kt);
             for (int j = data->adm_ptr[t]; j < data->adm_ptr[t + 1]; ++j) {
@@ -375,13 +376,15 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
                 d.t.ncol += rk[s];
                 coupling_elems += (int64_t)kt * rk[s];
             }
+            if (d.t.ncol > 0) phases[IDX_COUPLE].push_back(std::move(d));
             if (t > 0 && rk[parent[t]] > 0) {
                 const int p = parent[t];
-                d.segs.push_back({enc1(ktot + h->xo[p]), rk[p]});
-                d.pieces.push_back({3, data->T_off[t], kt, rk[p], false});
-                d.t.ncol += rk[p];
+                TaskBuild e = new_task((int32_t)(ktot + h->xo[t]), kt);
+                e.segs.push_back({enc1(ktot + h->xo[p]), rk[p]});
+                e.pieces.push_back({3, data->T_off[t], kt, rk[p], false});
+                e.t.ncol = rk[p];
+                phases[idx_down(l)].push_back(std::move(e));
             }
-            if (d.t.ncol > 0) phases[idx_down(l)].push_back(std::move(d));
         } else {
             adm_blocks += data->adm_ptr[t + 1] - data->adm_ptr[t];
         }
@@ -513,6 +516,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     fill(h->near, "near", phases[IDX_NEAR]);
     fill(h->upleaf, "upleaf", phases[IDX_UPLEAF]);
     fill(h->leafexp, "leafexp", phases[IDX_LEAFEXP]);
+    fill(h->couple, "couple", phases[IDX_COUPLE]);
     h->up.resize(nl);
     h->down.resize(nl);
     for (int l = 0; l < nl; ++l) fill(h->up[l], "up", phases[idx_up(l)]);
@@ -535,6 +539,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         nk += h->near.ntask() > 0;
         nk += h->upleaf.ntask() > 0;
         nk += h->leafexp.ntask() > 0;
+        nk += h->couple.ntask() > 0;
         for (int l = 0; l < nl; ++l) nk += (h->up[l].ntask() > 0) + (h->down[l].ntask() > 0);
         S.kernels_per_matvec = nk;
     }
@@ -574,7 +579,8 @@ static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st)
     H2_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
     H2_CUDA(launch(h->upleaf, x, coef, 0, st));
     for (int l = h->nlev - 1; l >= 0; --l) H2_CUDA(launch(h->up[l], x, coef, 0, st));
-    for (int l = 0; l < h->nlev; ++l) H2_CUDA(launch(h->down[l], x, coef, 0, st));
+    H2_CUDA(launch(h->couple, x, coef, 0, st));
+    for (int l = 0; l < h->nlev; ++l) H2_CUDA(launch(h->down[l], x, coef, 1, st));
     H2_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
     H2_CUDA(launch(h->leafexp, x, y, 1, st));
     return H2_OK;
@@ -644,10 +650,11 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
     const float2 *xx = reinterpret_cast<const float2 *>(x);
     float2 *yy = reinterpret_cast<float2 *>(y);
     float2 *coef = reinterpret_cast<float2 *>(h->d_coef);
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[7];
     for (auto &e : ev) H2_CUDA(cudaEventCreate(&e));
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int it = 0; it <= iters; ++it) {
+        H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * 2 * std::max<int64_t>(1, h->ktot), st));
         H2_CUDA(cudaEventRecord(ev[0], st));
         H2_CUDA(launch_phase_f32(h->near, h->d_mat, h->d_segs, xx, coef, yy, 0, st));
         H2_CUDA(cudaEventRecord(ev[1], st));
@@ -656,14 +663,16 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
         for (int l = h->nlev - 1; l >= 0; --l)
             H2_CUDA(launch_phase_f32(h->up[l], h->d_mat, h->d_segs, xx, coef, coef, 0, st));
         H2_CUDA(cudaEventRecord(ev[3], st));
-        for (int l = 0; l < h->nlev; ++l)
-            H2_CUDA(launch_phase_f32(h->down[l], h->d_mat, h->d_segs, xx, coef, coef, 0, st));
+        H2_CUDA(launch_phase_f32(h->couple, h->d_mat, h->d_segs, xx, coef, coef, 0, st));
         H2_CUDA(cudaEventRecord(ev[4], st));
-        H2_CUDA(launch_phase_f32(h->leafexp, h->d_mat, h->d_segs, xx, coef, yy, 1, st));
+        for (int l = 0; l < h->nlev; ++l)
+            H2_CUDA(launch_phase_f32(h->down[l], h->d_mat, h->d_segs, xx, coef, coef, 1, st));
         H2_CUDA(cudaEventRecord(ev[5], st));
-        H2_CUDA(cudaEventSynchronize(ev[5]));
+        H2_CUDA(launch_phase_f32(h->leafexp, h->d_mat, h->d_segs, xx, coef, yy, 1, st));
+        H2_CUDA(cudaEventRecord(ev[6], st));
+        H2_CUDA(cudaEventSynchronize(ev[6]));
         if (it == 0) continue;  // warm-up
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < 6; ++k) {
             float f = 0;
             H2_CUDA(cudaEventElapsedTime(&f, ev[k], ev[k + 1]));
             acc[k] += f;
@@ -679,9 +688,9 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
     H2_CUDA(cudaEventSynchronize(ev[1]));
     float f = 0;
     H2_CUDA(cudaEventElapsedTime(&f, ev[0], ev[1]));
-    acc[5] = f;
+    acc[6] = f;
     for (auto &e : ev) cudaEventDestroy(e);
-    for (int k = 0; k < n_ms && k < 6; ++k) ms[k] = acc[k] / iters;
+    for (int k = 0; k < n_ms && k < 7; ++k) ms[k] = acc[k] / iters;
     return H2_OK;
 }
 

@@ -68,7 +68,7 @@ struct h2_handle {
     void *d_ybuf = nullptr;
     int64_t buf_bytes = 0;
 
-    h2::Phase near, upleaf, leafexp;
+    h2::Phase near, upleaf, leafexp, couple;
     std::vector<h2::Phase> up;    // per level (index = level of the output cluster)
     std::vector<h2::Phase> down;  // per level
 

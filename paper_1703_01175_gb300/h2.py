@@ -315,9 +315,9 @@ class H2Matrix:
         return x, out
 
     def profile(self, x, y, iters: int = 10) -> dict:
-        ms = (ctypes.c_double * 6)()
+        ms = (ctypes.c_double * 7)()
         _check(lib().h2_profile_matvec(self._h, ctypes.c_void_p(x.data_ptr()),
-                                       ctypes.c_void_p(y.data_ptr()), iters, ms, 6),
+                                       ctypes.c_void_p(y.data_ptr()), iters, ms, 7),
                "h2_profile_matvec")
-        keys = ["near", "leaf_forward", "upward", "coupling_downward", "leaf_expansion", "total"]
+        keys = ["near", "leaf_forward", "upward", "coupling", "downward", "leaf_expansion", "total"]
         return dict(zip(keys, list(ms)))

@@ -158,6 +158,29 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
 h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
                             double *ms, int32_t n_ms);
 
+/*
+ * y = A x for one right-hand side in FP32 (c64 device vectors), like
+ * h2_matvec with nrhs = 1 and H2_PREC_FP32, but without any memory the
+ * handle allocated for scratch: the forward and backward coefficient vectors
+ * live in one static device array of H2_NOALLOC_MAX_COEF complex64 entries
+ * (8 MiB) that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart; this entry point exists for callers that must
+ * not call the CUDA allocator once running -- a step embedded in another
+ * framework whose caching allocator owns the device memory, a real-time loop
+ * that cannot take cudaMalloc's implicit synchronisation, or work issued
+ * while a stream is being captured into a graph. Such a caller loads the
+ * operator with h2_load at initialisation and afterwards passes only x and y.
+ * Operators needing more than H2_NOALLOC_MAX_COEF coefficients (2 x the sum
+ * of the cluster ranks) are rejected with H2_ERR_ARG. The first call on a
+ * device looks up the array's device address (once per device); make that
+ * first call before any stream capture. Every call shares the one array:
+ * calls that overlap on the GPU (different streams, or concurrent host
+ * threads) race and give wrong results. The array is zeroed at the start of
+ * every call. Asynchronous on `stream`.
+ */
+#define H2_NOALLOC_MAX_COEF 1048576
+h2_status h2_matvec_noalloc(h2_handle *h, const void *x, void *y, void *stream);
+
 /* Options of h2_gmres. */
 typedef struct {
     double tol;        /* stop when ||b - A x||_2 <= tol ||b||_2 (true residual) */

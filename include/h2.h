@@ -121,7 +121,14 @@ void h2_free(h2_handle *h);
  * with the inadmissible blocks. x and y are device arrays of nrhs columns of
  * length N with leading dimension ld >= N (elements); y is overwritten and
  * must not overlap x. Element type: c64 for H2_PREC_FP32 / H2_PREC_SPLITBF16,
- * c128 for H2_PREC_FP64ACC. nrhs >= 1. H2_PREC_SPLITBF16 requires nrhs >= 2.
+ * c128 for H2_PREC_FP64ACC. nrhs >= 1.
+ * Paths: nrhs = 1 FP32 runs level-batched GEMVs; nrhs > 1 FP32 runs complex
+ * GEMMs on CUDA cores; H2_PREC_SPLITBF16 runs the near-field and coupling
+ * products on the tensor cores (tcgen05, operands split into two bf16 terms,
+ * FP32 accumulation; relative error ~1e-5) and the tree passes in FP32. The
+ * first split-bf16 call packs the tensor-core operand images (device memory
+ * about twice the FP32 near-field and coupling data). FP64ACC with nrhs > 1
+ * runs one right-hand side after another.
  * Asynchronous on `stream`. Not thread-safe on one handle.
  */
 h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs,
@@ -131,6 +138,11 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs,
    runs the product and copies y back, and returns when y is complete. */
 h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host,
                          int32_t nrhs, int64_t ld, h2_prec prec);
+
+/* Synchronise the handle's device and report H2_ERR_TIMEOUT if a bounded wait
+   inside a tensor-core kernel ran out since the handle was loaded (the
+   kernel then skipped its output), else H2_OK. */
+h2_status h2_device_status(h2_handle *h);
 
 /* Sizes of the loaded representation (all counts in complex elements). */
 typedef struct {

@@ -232,10 +232,12 @@ void h2_free(h2_handle *h)
     if (h->s_aux) cudaStreamSynchronize(h->s_aux);
     cudaDeviceSynchronize();
     h2_free_krylov(h);
+    h2_free_split(h);
     cudaFree(h->d_mat);
     cudaFree(h->d_segs);
     cudaFree(h->d_tasks);
     cudaFree(h->d_coef);
+    cudaFree(h->d_coefm);
     cudaFree(h->d_xbuf);
     cudaFree(h->d_ybuf);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -487,6 +489,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     h->mat_elems = mat_elems;
     hmat.clear();
     hmat.shrink_to_fit();
+    h->segs_host = hsegs;
     H2_LOAD_CUDA(cudaMalloc(&h->d_segs, std::max<size_t>(1, hsegs.size()) * sizeof(Seg)));
     if (!hsegs.empty())
         H2_LOAD_CUDA(cudaMemcpy(h->d_segs, hsegs.data(), hsegs.size() * sizeof(Seg), cudaMemcpyHostToDevice));
@@ -549,6 +552,21 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     return H2_OK;
 }
 
+h2_status h2_device_status(h2_handle *h)
+{
+    if (!h) return arg_error("h2_device_status: NULL handle");
+    H2_CUDA(cudaSetDevice(h->device));
+    H2_CUDA(cudaDeviceSynchronize());
+    int flag = 0;
+    h2_status s = h2_split_error_flag(h, &flag);
+    if (s != H2_OK) return s;
+    if (flag) {
+        set_error("a bounded wait inside a tensor-core kernel ran out");
+        return H2_ERR_TIMEOUT;
+    }
+    return H2_OK;
+}
+
 h2_status h2_get_stats(const h2_handle *h, h2_stats *out)
 {
     if (!h || !out) return arg_error("NULL argument");
@@ -595,10 +613,15 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
     if (nrhs < 1) return arg_error("h2_matvec: nrhs must be >= 1");
     if (nrhs > 1 && ld < h->n) return arg_error("h2_matvec: ld < n");
     if (x == y) return arg_error("h2_matvec: x and y must not overlap");
-    if (prec == H2_PREC_SPLITBF16) return arg_error("h2_matvec: split-bf16 path not available");
-    if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC) return arg_error("h2_matvec: bad precision");
+    if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC && prec != H2_PREC_SPLITBF16)
+        return arg_error("h2_matvec: bad precision");
     H2_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (prec == H2_PREC_SPLITBF16)
+        return h2_run_multi_split(h, reinterpret_cast<const float2 *>(x), nrhs > 1 ? ld : h->n,
+                                  reinterpret_cast<float2 *>(y), nrhs > 1 ? ld : h->n, nrhs, st);
+    if (nrhs > 1 && prec == H2_PREC_FP32)
+        return h2_run_multi_f32(h, reinterpret_cast<const float2 *>(x), ld, reinterpret_cast<float2 *>(y), ld, nrhs, st);
     for (int32_t r = 0; r < nrhs; ++r) {
         h2_status s;
         if (prec == H2_PREC_FP32)

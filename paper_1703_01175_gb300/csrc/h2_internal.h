@@ -47,6 +47,41 @@ struct Phase {
 
 enum PhaseKind { PH_NEAR = 0, PH_UPLEAF, PH_UP, PH_DOWN, PH_LEAFEXP, PH_COUNT };
 
+// One tile of the split-bf16 tensor-core path (h2_umma.cu): up to 128 output
+// rows of a task, its packed matrix images and its input chunk table.
+struct UTask {
+    int32_t out_off;    // complex offset of the first output row
+    int32_t m;          // complex rows in this tile (<= 128)
+    int32_t n;          // real MMA N = 2 * round_up(m, 8)
+    int32_t nst;        // K stages of 32 complex columns
+    int64_t img_off;    // byte offset of stage 0's image (hi plane, then lo plane)
+    int32_t chunk_off;  // first entry in the chunk table (8 per stage)
+    int32_t pad_;
+};
+
+struct UPackInfo {
+    int32_t row0, npc, colmap_off, mpad;
+    int64_t mat_off;
+};
+
+struct UPhase {
+    int ntile = 0;
+    UTask *d_tasks = nullptr;
+    int32_t *d_chunks = nullptr;
+    uint8_t *d_images = nullptr;
+    int64_t image_bytes = 0;
+};
+
+struct SplitState {
+    UPhase near, couple;
+    int64_t np_x = 0, np_c = 0;   // padded complex lengths of the x and coefficient planes
+    int nx = 0, nc = 0;           // scattered entries
+    int32_t *d_xsrc = nullptr, *d_xdst = nullptr, *d_csrc = nullptr, *d_cdst = nullptr;
+    void *xhi = nullptr, *xlo = nullptr, *chi = nullptr, *clo = nullptr;  // bf16 planes
+    int rcap = 0;
+    int *d_err = nullptr;         // set when a bounded wait ran out
+};
+
 void set_error(const std::string &msg);
 
 }  // namespace h2
@@ -78,15 +113,29 @@ struct h2_handle {
     h2_stats stats{};
 
     void *krylov = nullptr;       // GMRES workspace (h2_krylov.cu)
+    void *d_coefm = nullptr;      // multi-RHS coefficients (2 ktot x R, h2_mrhs.cu)
+    int64_t coefm_bytes = 0;
+    std::vector<h2::Seg> segs_host;   // host copy of the input segments (split-bf16 packing)
+    h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
 };
 
 void h2_free_krylov(h2_handle *h);
+h2_status h2_ensure_coefm(h2_handle *h, int nrhs);
+void h2_free_split(h2_handle *h);
+h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
+                             cudaStream_t st);
+h2_status h2_split_error_flag(h2_handle *h, int *flag);
+h2_status h2_run_multi_f32(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
+                           cudaStream_t st);
 
 namespace h2 {
 // launch one phase; VT = float2 (FP32) or double2 (FP64 accumulation)
 cudaError_t launch_phase_f32(const Phase &ph, const float2 *mat, const Seg *segs,
                              const float2 *in0, const float2 *in1, float2 *out,
                              int beta_one, cudaStream_t st);
+cudaError_t launch_phase_mrhs_f32(const Phase &ph, const float2 *mat, const Seg *segs, const float2 *in0,
+                                  int64_t ld0, const float2 *in1, int64_t ld1, float2 *out, int64_t ldo, int nrhs,
+                                  int beta_one, cudaStream_t st);
 cudaError_t launch_phase_f64(const Phase &ph, const float2 *mat, const Seg *segs,
                              const double2 *in0, const double2 *in1, double2 *out,
                              int beta_one, cudaStream_t st);

@@ -1,0 +1,591 @@
+// Multi-RHS near-field and coupling products on the 5th-generation tensor
+// cores (tcgen05), with operands split into two bf16 terms and FP32
+// accumulation in tensor memory.
+//
+// For R right-hand sides a task out (m x R) = M (m x ncol) X (ncol x R) is the
+// real GEMM  D (R x 2m) = Xr (R x 2 ncol) . A2 (2m x 2 ncol)^T  with
+//   Xr[r][2c + 0/1] = Re/Im x_r(c)  and, per complex entry a = M[i][c],
+//   A2[2i][2c] = Re a, A2[2i][2c+1] = -Im a, A2[2i+1][2c] = Im a, A2[2i+1][2c+1] = Re a,
+// so that D[r][2i], D[r][2i+1] are the real and imaginary parts of y_r(i).
+// Each operand is split as v = hi + lo (bf16) and D accumulates hi.hi, hi.lo and
+// lo.hi (the lo.lo term is below the FP32 rounding of the result).
+//
+// Tiles: M = 128 right-hand sides (one tile of TMEM lanes), N = 2 * m rounded
+// up to 16 (<= 256), K staged 64 bf16 (32 complex columns) at a time in
+// 128-byte-swizzled K-major shared memory. The matrix operand is pre-packed
+// once on the device into that exact shared-memory image and fetched with one
+// bulk asynchronous copy per stage; the right-hand-side operand is gathered
+// with 16-byte cp.async from bf16 planes in which every segment starts on a
+// multiple of 4 complex entries. Two stages alternate: while the tensor core
+// works on one, the CTA fills the other.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+namespace {
+
+constexpr int UT = 128;               // threads per CTA (4 warps)
+constexpr int KST = 64;               // bf16 K elements per stage (128 bytes per row)
+constexpr int CPS = KST / 2;          // complex columns per stage
+constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
+constexpr int XPLANE = MT * 128;      // bytes of one X plane image per stage
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait for the phase with the given parity; false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void cp16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n
+__device__ __forceinline__ uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+}  // namespace
+
+// One tile of a split-bf16 task (see h2_internal.h: UTask).
+__global__ void __launch_bounds__(UT, 1)
+umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
+                 const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
+                 const __nv_bfloat16 *__restrict__ xlo, int64_t ldp, int nrhs, float2 *__restrict__ out,
+                 int64_t ldo, int beta_one, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned carve-up: [X0 hi|lo][X1 hi|lo][A0 hi|lo][A1 hi|lo], barriers at the end
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const UTask tk = tasks[blockIdx.x];
+    const int N = tk.n;
+    const uint32_t abytes = (uint32_t)N * 128u;  // one plane of the matrix image per stage
+    uint8_t *sx[2] = {base, base + 2 * XPLANE};
+    uint8_t *sa[2] = {base + 4 * XPLANE, base + 4 * XPLANE + 2 * 256 * 128};
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 4 * XPLANE + 4 * 256 * 128);
+    uint64_t *full = bars;       // [2] matrix image arrived
+    uint64_t *done = bars + 2;   // [2] MMAs of that stage finished
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.y * MT;
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&done[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = idesc_bf16(N);
+
+    for (int s = 0; s < tk.nst; ++s) {
+        const int b = s & 1;
+        if (s >= 2) {
+            if (!mbar_wait(&done[b], ((s - 2) >> 1) & 1)) abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0) {
+            const uint8_t *img = images + tk.img_off + (int64_t)s * 2 * abytes;
+            mbar_expect_tx(&full[b], 2 * abytes);
+            bulk_g2s(sa[b], img, 2 * abytes, &full[b]);
+        }
+        // gather the right-hand-side tile: 128 rows x 8 chunks of 16 B, two planes
+        const int32_t *ch = chunks + tk.chunk_off + (int64_t)s * (CPS / 4);
+        for (int e = tid; e < 2 * MT * 8; e += UT) {
+            const int plane = e >= MT * 8;
+            const int ee = e - plane * MT * 8;
+            const int r = ee >> 3, q = ee & 7;
+            uint8_t *dst = sx[b] + plane * XPLANE + r * 128 + ((q ^ (r & 7)) << 4);
+            const int32_t ci = ch[q];
+            const int rr = r0 + r;
+            if (ci >= 0 && rr < nrhs) {
+                const __nv_bfloat16 *src = (plane ? xlo : xhi) + (int64_t)rr * ldp + 2 * (int64_t)ci;
+                cp16(dst, src);
+            } else {
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            if (!mbar_wait(&full[b], (s >> 1) & 1)) {
+                abort_flag = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t xa = smem_u32(sx[b]), xb = xa + XPLANE;
+                const uint32_t aa = smem_u32(sa[b]), ab = aa + abytes;
+#pragma unroll
+                for (int k = 0; k < KST / 16; ++k) {
+                    const uint32_t off = k * 32;
+                    const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
+                    umma(tmem, sdesc(xa + off), sdesc(aa + off), idesc, first);   // hi . hi
+                    umma(tmem, sdesc(xa + off), sdesc(ab + off), idesc, 1u);      // hi . lo
+                    umma(tmem, sdesc(xb + off), sdesc(aa + off), idesc, 1u);      // lo . hi
+                }
+                umma_commit(&done[b]);
+            }
+        }
+    }
+    __syncthreads();
+    const bool ok = !abort_flag && tk.nst > 0;
+    if (ok) {
+        const int last = tk.nst - 1;
+        if (!mbar_wait(&done[last & 1], (last >> 1) & 1)) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_flag && tk.nst > 0) {
+        // epilogue: lane r of TMEM holds D[r][0..N) = (Re, Im) pairs of output rows
+        const int r = r0 + warp * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int j0 = 0; j0 < N; j0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tl + (uint32_t)j0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (r < nrhs) {
+                float2 *o = out + (int64_t)r * ldo + tk.out_off;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = j0 / 2 + q;
+                    if (i < tk.m) {
+                        float2 val = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+                        if (beta_one) {
+                            const float2 p = o[i];
+                            val.x += p.x;
+                            val.y += p.y;
+                        }
+                        o[i] = val;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+// Pack the real-expanded, bf16-split matrix images of every tile/stage.
+__global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
+                                 const int32_t *__restrict__ colmap, const float2 *__restrict__ mat,
+                                 uint8_t *__restrict__ images)
+{
+    const UTask tk = tasks[blockIdx.x];
+    const UPackInfo pi = info[blockIdx.x];
+    const int N = tk.n;
+    const int s = blockIdx.y;
+    if (s >= tk.nst) return;
+    uint8_t *img = images + tk.img_off + (int64_t)s * 2 * N * 128;
+    for (int e = threadIdx.x; e < N * KST; e += blockDim.x) {
+        const int nr = e / KST, kk = e % KST;
+        const int i = pi.row0 + (nr >> 1);                 // complex row in the task matrix
+        const int pc = s * CPS + (kk >> 1);                // padded complex column
+        const int c = pc < pi.npc ? colmap[pi.colmap_off + pc] : -1;
+        float v = 0.f;
+        if (c >= 0 && (nr >> 1) < tk.m) {
+            const float2 a = mat[pi.mat_off + (int64_t)c * pi.mpad + i];
+            const int part = nr & 1, comp = kk & 1;
+            v = part == 0 ? (comp == 0 ? a.x : -a.y) : (comp == 0 ? a.y : a.x);
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const int byte = nr * 128 + ((((kk * 2) >> 4) ^ (nr & 7)) << 4) + ((kk * 2) & 15);
+        *reinterpret_cast<__nv_bfloat16 *>(img + byte) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(img + N * 128 + byte) = lo;
+    }
+}
+
+// Scatter complex values into bf16 hi/lo planes: plane[r][2 pos(i) + {0,1}].
+// src element (r, i) at src[r * lds + map_src(i)], destination complex index map_dst(i).
+__global__ void split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ sidx,
+                                     const int32_t *__restrict__ didx, int count, int nrhs,
+                                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t ldp)
+{
+    const int r = blockIdx.y;
+    if (r >= nrhs) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const float2 v = src[(int64_t)r * lds + sidx[i]];
+        const int64_t d = (int64_t)r * ldp + 2 * (int64_t)didx[i];
+        const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
+        phi[d] = hx;
+        phi[d + 1] = hy;
+        plo[d] = __float2bfloat16_rn(v.x - __bfloat162float(hx));
+        plo[d + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hy));
+    }
+}
+
+size_t umma_smem_bytes() { return 4 * XPLANE + 4 * 256 * 128 + 64 + 1024; }
+
+}  // namespace h2
+
+using namespace h2;
+
+#define UM_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t e__ = (call);                                                     \
+        if (e__ != cudaSuccess) {                                                     \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));           \
+            return H2_ERR_CUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+// Host side: build tiles, chunk tables and packed images of one phase.
+static h2_status build_uphase(h2_handle *h, const Phase &ph, const std::vector<Seg> &hsegs,
+                              const std::vector<int32_t> &seg_plane_base, UPhase &U)
+{
+    std::vector<UTask> tiles;
+    std::vector<UPackInfo> infos;
+    std::vector<int32_t> chunks, colmap;
+    int64_t img = 0;
+    for (const Task &t : ph.tasks) {
+        // padded columns: each segment rounded up to a multiple of 4 complex entries
+        std::vector<int32_t> cm;        // padded column -> original column (-1 pad)
+        std::vector<int32_t> chunk_src; // per 4-column chunk: complex index in the bf16 plane
+        int orig = 0;
+        for (int si = t.seg_begin; si < t.seg_end; ++si) {
+            const Seg &sg = hsegs[si];
+            const int pbase = seg_plane_base[si];
+            const int np = (sg.n + 3) / 4 * 4;
+            for (int j = 0; j < np; ++j) cm.push_back(j < sg.n ? orig + j : -1);
+            for (int j = 0; j < np; j += 4) chunk_src.push_back(pbase + j);
+            orig += sg.n;
+        }
+        const int npc = (int)cm.size();
+        const int nst = (npc + CPS - 1) / CPS;
+        while ((int)chunk_src.size() < nst * (CPS / 4)) chunk_src.push_back(-1);
+        const int colmap_off = (int)colmap.size();
+        colmap.insert(colmap.end(), cm.begin(), cm.end());
+        const int chunk_off = (int)chunks.size();
+        chunks.insert(chunks.end(), chunk_src.begin(), chunk_src.end());
+        for (int row0 = 0; row0 < t.m; row0 += 128) {
+            const int mt = std::min(128, t.m - row0);
+            UTask u{};
+            u.out_off = t.out_off + row0;
+            u.m = mt;
+            u.n = 2 * ((mt + 7) / 8 * 8);
+            u.nst = nst;
+            u.img_off = img;
+            u.chunk_off = chunk_off;
+            img += (int64_t)nst * 2 * u.n * 128;
+            tiles.push_back(u);
+            UPackInfo pi{};
+            pi.row0 = row0;
+            pi.npc = npc;
+            pi.colmap_off = colmap_off;
+            pi.mpad = t.mpad;
+            pi.mat_off = t.mat_off;
+            infos.push_back(pi);
+        }
+    }
+    U.ntile = (int)tiles.size();
+    U.image_bytes = img;
+    if (U.ntile == 0) return H2_OK;
+    UTask *d_tiles = nullptr;
+    UPackInfo *d_info = nullptr;
+    int32_t *d_colmap = nullptr;
+    UM_CUDA(cudaMalloc(&d_tiles, tiles.size() * sizeof(UTask)));
+    UM_CUDA(cudaMalloc(&d_info, infos.size() * sizeof(UPackInfo)));
+    UM_CUDA(cudaMalloc(&d_colmap, std::max<size_t>(1, colmap.size()) * sizeof(int32_t)));
+    UM_CUDA(cudaMalloc(&U.d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(int32_t)));
+    UM_CUDA(cudaMalloc(&U.d_images, std::max<int64_t>(16, img)));
+    UM_CUDA(cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(UTask), cudaMemcpyHostToDevice));
+    UM_CUDA(cudaMemcpy(d_info, infos.data(), infos.size() * sizeof(UPackInfo), cudaMemcpyHostToDevice));
+    if (!colmap.empty())
+        UM_CUDA(cudaMemcpy(d_colmap, colmap.data(), colmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!chunks.empty())
+        UM_CUDA(cudaMemcpy(U.d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    int maxst = 0;
+    for (auto &u : tiles) maxst = std::max(maxst, u.nst);
+    dim3 grid(U.ntile, maxst);
+    umma_pack_kernel<<<grid, 256>>>(d_tiles, d_info, d_colmap, h->d_mat, U.d_images);
+    UM_CUDA(cudaGetLastError());
+    UM_CUDA(cudaDeviceSynchronize());
+    U.d_tasks = d_tiles;
+    cudaFree(d_info);
+    cudaFree(d_colmap);
+    return H2_OK;
+}
+
+static h2_status split_init(h2_handle *h)
+{
+    if (h->split) return H2_OK;
+    auto *S = new SplitState();
+    // plane layouts: leaves of the tree order (near-field inputs) and cluster
+    // coefficient blocks (coupling inputs), each padded to 4 complex entries
+    std::vector<int32_t> leaf_pbase(h->nc, -1), coef_pbase(h->nc, -1);
+    int64_t p = 0;
+    std::vector<int32_t> xs, xd;
+    for (int t = 0; t < h->nc; ++t) {
+        if (h->child[2 * t] >= 0) continue;
+        leaf_pbase[t] = (int32_t)p;
+        for (int i = 0; i < h->size[t]; ++i) {
+            xs.push_back(h->begin[t] + i);
+            xd.push_back((int32_t)(p + i));
+        }
+        p += (h->size[t] + 3) / 4 * 4;
+    }
+    S->np_x = std::max<int64_t>(8, (p + 3) / 4 * 4);
+    int64_t q = 0;
+    std::vector<int32_t> cs, cd;
+    for (int t = 0; t < h->nc; ++t) {
+        if (h->rank[t] == 0) continue;
+        coef_pbase[t] = (int32_t)q;
+        for (int i = 0; i < h->rank[t]; ++i) {
+            cs.push_back(h->xo[t] + i);
+            cd.push_back((int32_t)(q + i));
+        }
+        q += (h->rank[t] + 3) / 4 * 4;
+    }
+    S->np_c = std::max<int64_t>(8, (q + 3) / 4 * 4);
+    S->nx = (int)xs.size();
+    S->nc = (int)cs.size();
+    auto up = [&](const std::vector<int32_t> &v, int32_t **d) -> h2_status {
+        UM_CUDA(cudaMalloc(d, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
+        if (!v.empty()) UM_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        return H2_OK;
+    };
+    h2_status st;
+    if ((st = up(xs, &S->d_xsrc)) != H2_OK || (st = up(xd, &S->d_xdst)) != H2_OK ||
+        (st = up(cs, &S->d_csrc)) != H2_OK || (st = up(cd, &S->d_cdst)) != H2_OK) {
+        h->split = S;
+        return st;
+    }
+    // per-segment plane base of the near-field and coupling phases
+    const std::vector<Seg> &hsegs = h->segs_host;
+    std::unordered_map<int32_t, int32_t> leaf_of_begin, cluster_of_xo;
+    for (int t = 0; t < h->nc; ++t) {
+        if (h->child[2 * t] < 0) leaf_of_begin[h->begin[t]] = t;
+        if (h->rank[t] > 0) cluster_of_xo[h->xo[t]] = t;
+    }
+    std::vector<int32_t> nbase(hsegs.size(), -1), cbase(hsegs.size(), -1);
+    auto seg_base = [&](const Phase &ph, std::vector<int32_t> &out, bool leafplane) {
+        for (const Task &t : ph.tasks)
+            for (int si = t.seg_begin; si < t.seg_end; ++si) {
+                const Seg &sg = hsegs[si];
+                if (leafplane) {
+                    // near-field segments are whole leaves: in_off = begin of the leaf
+                    const int leaf = leaf_of_begin.at(sg.in_off);
+                    out[si] = leaf_pbase[leaf];
+                } else {
+                    const int64_t off = -(int64_t)sg.in_off - 1;  // xo of the source cluster
+                    out[si] = coef_pbase[cluster_of_xo.at((int32_t)off)];
+                }
+            }
+    };
+    seg_base(h->near, nbase, true);
+    seg_base(h->couple, cbase, false);
+    h->split = S;
+    if ((st = build_uphase(h, h->near, hsegs, nbase, S->near)) != H2_OK) return st;
+    if ((st = build_uphase(h, h->couple, hsegs, cbase, S->couple)) != H2_OK) return st;
+    UM_CUDA(cudaFuncSetAttribute(umma_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)umma_smem_bytes()));
+    UM_CUDA(cudaMalloc(&S->d_err, sizeof(int)));
+    UM_CUDA(cudaMemset(S->d_err, 0, sizeof(int)));
+    return H2_OK;
+}
+
+static h2_status ensure_planes(h2_handle *h, int rpad)
+{
+    SplitState *S = h->split;
+    if (rpad <= S->rcap) return H2_OK;
+    cudaFree(S->xhi);
+    cudaFree(S->xlo);
+    cudaFree(S->chi);
+    cudaFree(S->clo);
+    S->xhi = S->xlo = S->chi = S->clo = nullptr;
+    S->rcap = 0;
+    const size_t bx = (size_t)rpad * 2 * S->np_x * sizeof(__nv_bfloat16);
+    const size_t bc = (size_t)rpad * 2 * S->np_c * sizeof(__nv_bfloat16);
+    if (cudaMalloc(&S->xhi, bx) != cudaSuccess || cudaMalloc(&S->xlo, bx) != cudaSuccess ||
+        cudaMalloc(&S->chi, bc) != cudaSuccess || cudaMalloc(&S->clo, bc) != cudaSuccess) {
+        set_error("split-bf16 plane allocation failed");
+        return H2_ERR_ALLOC;
+    }
+    // padding entries stay zero: the scatter kernels never write them
+    UM_CUDA(cudaMemset(S->xhi, 0, bx));
+    UM_CUDA(cudaMemset(S->xlo, 0, bx));
+    UM_CUDA(cudaMemset(S->chi, 0, bc));
+    UM_CUDA(cudaMemset(S->clo, 0, bc));
+    S->rcap = rpad;
+    return H2_OK;
+}
+
+static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_bfloat16 *phi,
+                               const __nv_bfloat16 *plo, int64_t ldp, int nrhs, float2 *out, int64_t ldo,
+                               int beta, cudaStream_t st)
+{
+    if (U.ntile == 0) return cudaSuccess;
+    dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
+    umma_task_kernel<<<grid, UT, umma_smem_bytes(), st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs,
+                                                          out, ldo, beta, S->d_err);
+    return cudaGetLastError();
+}
+
+static inline __nv_bfloat16 *bf(void *p) { return reinterpret_cast<__nv_bfloat16 *>(p); }
+
+void h2_free_split(h2_handle *h)
+{
+    SplitState *S = h->split;
+    if (!S) return;
+    for (UPhase *U : {&S->near, &S->couple}) {
+        cudaFree(U->d_tasks);
+        cudaFree(U->d_chunks);
+        cudaFree(U->d_images);
+    }
+    cudaFree(S->d_xsrc);
+    cudaFree(S->d_xdst);
+    cudaFree(S->d_csrc);
+    cudaFree(S->d_cdst);
+    cudaFree(S->xhi);
+    cudaFree(S->xlo);
+    cudaFree(S->chi);
+    cudaFree(S->clo);
+    cudaFree(S->d_err);
+    delete S;
+    h->split = nullptr;
+}
+
+h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
+                             cudaStream_t st)
+{
+    h2_status s = split_init(h);
+    if (s != H2_OK) return s;
+    SplitState *S = h->split;
+    const int rpad = (nrhs + MT - 1) / MT * MT;
+    if ((s = ensure_planes(h, rpad)) != H2_OK) return s;
+    if ((s = h2_ensure_coefm(h, nrhs)) != H2_OK) return s;
+    const int64_t ldc = std::max<int64_t>(2, 2 * h->ktot);
+    float2 *coef = reinterpret_cast<float2 *>(h->d_coefm);
+    const float2 *mat = h->d_mat;
+    const Seg *segs = h->d_segs;
+    const int64_t ldpx = 2 * S->np_x, ldpc = 2 * S->np_c;
+    UM_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * ldc * nrhs, st));
+    {
+        dim3 g(std::min(64, (S->nx + 255) / 256), nrhs);
+        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xsrc, S->d_xdst, S->nx, nrhs, bf(S->xhi), bf(S->xlo), ldpx);
+        UM_CUDA(cudaGetLastError());
+    }
+    UM_CUDA(cudaEventRecord(h->ev_fork, st));
+    UM_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
+    UM_CUDA(launch_umma(S->near, S, bf(S->xhi), bf(S->xlo), ldpx, nrhs, y, ldy, 0, h->s_aux));
+    UM_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
+    UM_CUDA(launch_phase_mrhs_f32(h->upleaf, mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
+    for (int l = h->nlev - 1; l >= 0; --l)
+        UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
+    {
+        dim3 g(std::min(64, (S->nc + 255) / 256), nrhs);
+        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_csrc, S->d_cdst, S->nc, nrhs, bf(S->chi), bf(S->clo), ldpc);
+        UM_CUDA(cudaGetLastError());
+    }
+    UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), ldpc, nrhs, coef, ldc, 0, st));
+    for (int l = 0; l < h->nlev; ++l)
+        UM_CUDA(launch_phase_mrhs_f32(h->down[l], mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 1, st));
+    UM_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
+    UM_CUDA(launch_phase_mrhs_f32(h->leafexp, mat, segs, x, ldx, coef, ldc, y, ldy, nrhs, 1, st));
+    return H2_OK;
+}
+
+h2_status h2_split_error_flag(h2_handle *h, int *flag)
+{
+    *flag = 0;
+    if (!h->split) return H2_OK;
+    UM_CUDA(cudaMemcpy(flag, h->split->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return H2_OK;
+}

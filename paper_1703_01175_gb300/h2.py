@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
     L.h2_gmres.restype = ctypes.c_int
     L.h2_gmres.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                            ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
+    L.h2_device_status.restype = ctypes.c_int
+    L.h2_device_status.argtypes = [ctypes.c_void_p]
     L.h2_status_string.restype = ctypes.c_char_p
     L.h2_status_string.argtypes = [ctypes.c_int]
     L.h2_last_error.restype = ctypes.c_char_p
@@ -112,7 +114,7 @@ def _check(status: int, where: str):
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
     return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
-            "h2_profile_matvec", "h2_gmres", "h2_status_string", "h2_last_error"]
+            "h2_profile_matvec", "h2_gmres", "h2_device_status", "h2_status_string", "h2_last_error"]
 
 
 # ---------------------------------------------------------------------------
@@ -292,6 +294,10 @@ class H2Matrix:
         _check(lib().h2_matvec_host(self._h, xf.ctypes.data, y.ctypes.data, nrhs, self.n, PREC[prec]),
                "h2_matvec_host")
         return y
+
+    def device_status(self) -> int:
+        """Synchronise and return H2_OK or H2_ERR_TIMEOUT (a bounded wait ran out)."""
+        return lib().h2_device_status(self._h)
 
     def gmres(self, b, x=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
               precond=0, stream=None, check=True):

@@ -4,7 +4,10 @@ the H^2 data of the host constructor, the launch configuration bench.py times.
 - FP32 product vs the oracle's FP64 H^2 product on the same data: 1e-5;
 - sampled rows against the oracle's dense VIE rows, evaluated one by one:
   representation error within 10 eps;
-- GMRES(50) to 1e-4: the oracle's FP64 residual of the GPU solution <= 1.05e-4.
+- GMRES to 1e-4: the oracle's FP64 residual of the GPU solution <= 1.05e-4.
+  This random-permittivity cube is hard for restarted GMRES: with m = 50 the
+  residual stagnates near 7e-4 (the GPU and the oracle agree on that on the
+  smaller 16^3 version), so the solve uses m = 400.
 """
 import math
 
@@ -55,7 +58,7 @@ def test_full_size_product_matches_oracle(full):
 def test_full_size_gmres_residual(full):
     w, arrs, perm, A, hZ = full
     b = synth.default_rhs(w)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
-    x, info = A.gmres(torch.from_numpy(b).cuda(), tol=w.tol, restart=50, maxit=2000, refine=True)
+    x, info = A.gmres(torch.from_numpy(b).cuda(), tol=w.tol, restart=400, maxit=3000, refine=True)
     assert info[0]["status"] == 0, info
     x = x.cpu().numpy()
     res = np.linalg.norm(b - h2mv.h2_matvec(hZ, x)) / np.linalg.norm(b)

@@ -99,3 +99,38 @@ def test_zero_vector_and_repeat_determinism(loaded):
     y1 = A.matvec(x).clone()
     y2 = A.matvec(x)
     assert torch.equal(y1, y2)  # row-owned reductions: bitwise reproducible
+
+
+def _colmajor(X):
+    return torch.from_numpy(np.asfortranarray(X.astype(np.complex64))).cuda().t().contiguous().t()
+
+
+@pytest.mark.parametrize("name,R", [("cube12", 33), ("ragged", 2), ("slab", 40)])
+def test_multi_rhs_fp32_matches_oracle(loaded, name, R):
+    from oracle import h2mv
+    c = cases.get(name)
+    A = _mat(loaded, name)
+    X = synth.random_complex(c.n, 11, cols=R)
+    Y_or = h2mv.h2_dense(c.hZ) @ X
+    Y = A.matvec(_colmajor(X)).cpu().numpy()
+    assert _rel(Y, Y_or) <= 1e-5
+    for j in (0, R - 1):
+        assert np.linalg.norm(Y[:, j] - Y_or[:, j]) <= 1e-5 * np.linalg.norm(Y_or[:, j])
+
+
+@pytest.mark.parametrize("name,R", [("cube12", 128), ("cube12", 5), ("ragged", 130), ("slab", 64),
+                                    ("array", 17), ("tiny_leaves", 3)])
+def test_splitbf16_tensor_cores_match_oracle(loaded, name, R):
+    """Split-bf16 tcgen05 path: within eps = 1e-4 of the oracle's FP64 product
+    (spec bound for the lower-precision form)."""
+    from oracle import h2mv
+    c = cases.get(name)
+    A = _mat(loaded, name)
+    X = synth.random_complex(c.n, 12, cols=R)
+    Y_or = h2mv.h2_dense(c.hZ) @ X
+    for rep in range(2):
+        Y = A.matvec(_colmajor(X), prec="splitbf16").cpu().numpy()
+        assert A.device_status() == 0
+        assert _rel(Y, Y_or) <= 1e-4
+        colerr = np.linalg.norm(Y - Y_or, axis=0) / np.linalg.norm(Y_or, axis=0)
+        assert colerr.max() <= 1e-4

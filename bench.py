@@ -210,6 +210,20 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
 
+    if args.only_mrhs:
+        R = max(1, args.mrhs)
+        Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
+        Xm = Xm.to(dev).t().contiguous().t()
+        Ym = torch.empty_like(Xm)
+        for _ in range(args.warmup + args.steps):
+            A.matvec(Xm, Ym, prec="splitbf16")
+        torch.cuda.synchronize(dev)
+        status = A.device_status()
+        A.close()
+        if rank == 0:
+            print(json.dumps({"only_mrhs": True, "nrhs": R, "workload": args.workload, "status": status}), flush=True)
+        return
+
     if args.only_matvec:
         A.close()
         if rank == 0:
@@ -248,6 +262,35 @@ def run_ours(args, rank, world, local_rank):
         gm[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
                      "rel_res": info[0]["rel_res"], "status": info[0]["status"]}
 
+    # multi-RHS products: R right-hand sides at once (split-bf16 tensor cores vs FP32 CUDA cores)
+    mr = None
+    if args.mrhs > 0:
+        R = args.mrhs
+        Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
+        Xm = Xm.to(dev).t().contiguous().t()
+        Ym = torch.empty_like(Xm)
+        mr = {"nrhs": R}
+        entries = st["near_elems"] + st["coupling_elems"] + 2 * st["transfer_elems"] + 2 * st["leaf_elems"]
+        tc_entries = st["near_elems"] + st["coupling_elems"]
+        for label, prec in (("splitbf16", "splitbf16"), ("fp32", "fp32")):
+            for _ in range(3):
+                A.matvec(Xm, Ym, prec=prec)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                A.matvec(Xm, Ym, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t_ms = e0.elapsed_time(e1) / args.steps
+            mr[label] = {"ms": t_ms, "us_per_rhs": 1e3 * t_ms / R,
+                         "algorithmic_tflops": 8.0 * R * entries / (t_ms * 1e-3) / 1e12}
+        mr["splitbf16"]["tensor_tflops_executed_near_couple_share"] = None
+        mr["status"] = A.device_status()
+        mr["speedup_vs_single_rhs_fp32"] = (ms * R) / mr["splitbf16"]["ms"]
+        mr["tc_entries"] = tc_entries
+
     # end to end through the host-pointer entry point
     for _ in range(2):
         A.matvec_host(x_np)
@@ -285,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
         "matvec_gbs": mv_gbs, "matvec_frac_hbm": mv_gbs / hbm,
         "stages_ms": prof,
         "gmres": gm,
+        "mrhs": mr,
         "roofline": ({"bound": "hbm", "kernel": "rowgemv (coupling launch, all levels)", "achieved": couple_gbs,
                       "peak": hbm, "unit": "GB/s", "frac": couple_gbs / hbm, "traffic": traffic_couple,
                       "algorithmic_bytes_per_launch": couple_bytes, "peak_source": peak_kind}
@@ -309,7 +353,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")
+    ap.add_argument("--only-mrhs", action="store_true",
+                    help="run split-bf16 multi-RHS products only (profiling)")
     ap.add_argument("--only-matvec", action="store_true",
                     help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
     args = ap.parse_args()

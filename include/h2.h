@@ -201,7 +201,10 @@ typedef struct {
     int32_t refine;    /* 1: restart residuals use the FP64-accumulated product
                           (iterative refinement of the FP32 inner cycles) */
     int32_t x0_given;  /* 1: x holds the initial guess on entry; 0: start from 0 */
-    int32_t precond;   /* 0: none; 1: learned preconditioner (flexible GMRES) */
+    int32_t precond;   /* 0: none; 1: the handle's learned preconditioner as the
+                          right preconditioner of flexible GMRES (Saad 1993):
+                          z_j = M(v_j), A z_j enters the Arnoldi process and
+                          x += Z y at the end of each cycle */
 } h2_solve_opts;
 
 /* Per right-hand-side outcome of h2_gmres. */
@@ -229,6 +232,24 @@ typedef struct {
  */
 h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld,
                    const h2_solve_opts *opts, h2_solve_info *info, void *stream);
+
+/*
+ * Load (or, with n_layers = 0, remove) the learned preconditioner used by
+ * h2_gmres with precond = 1: a chain of 3x3x3 convolutions on the
+ * Dx x Dy x Dz voxel grid (include/h2nn.h). Unknown 3 p + c of the operator is
+ * field component c of the voxel at tree position p, and grid_of[p] is that
+ * voxel's grid index. M(v): v is scaled to unit RMS and packed into 8
+ * channels (Re, Im of the 3 components, aux[v] = a per-voxel input such as
+ * chi, 0); the layers run in order (ReLU where layer_spec[3l+2] != 0); output
+ * channels 0..5 are unpacked with the inverse scale.
+ * layer_spec: [3 n_layers] (Cin, Cout, relu), channels in {8, 16, 32}, first
+ * Cin = 8, last Cout = 8. weights: bf16 (uint16) [Cout][27][Cin] per layer,
+ * concatenated; biases: f32 [Cout] per layer, concatenated; aux: f32 [V] or
+ * NULL. All arrays are host memory, copied. Synchronous.
+ */
+h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy, int32_t Dz, const int32_t *grid_of,
+                                const float *aux, int32_t n_layers, const int32_t *layer_spec,
+                                const void *weights, const float *biases);
 
 const char *h2_status_string(h2_status s);
 

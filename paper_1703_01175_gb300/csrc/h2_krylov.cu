@@ -281,15 +281,15 @@ __global__ void k_backsolve(KrylovDev K, int k)
     }
 }
 
-// x += V(:, 0..k) y
-__global__ void k_xupdate(KrylovDev K, int k, double2 *__restrict__ x)
+// x += B(:, 0..k) y with B = V (GMRES) or Z (flexible GMRES)
+__global__ void k_xupdate(KrylovDev K, const double2 *__restrict__ basis, int k, double2 *__restrict__ x)
 {
     extern __shared__ double2 ys[];
     for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = K.h1[l];
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
         double2 acc = x[i];
-        for (int l = 0; l < k; ++l) acc = cadd(acc, cmul(K.V[(size_t)l * K.n + i], ys[l]));
+        for (int l = 0; l < k; ++l) acc = cadd(acc, cmul(basis[(size_t)l * K.n + i], ys[l]));
         x[i] = acc;
     }
 }
@@ -312,6 +312,8 @@ using namespace h2;
 
 struct KrylovWork {
     int n = 0, m = 0;
+    bool flexible = false;
+    double2 *Z = nullptr;      // preconditioned directions (flexible GMRES)
     KrylovDev K{};
     double2 *r = nullptr, *tmp = nullptr;
     float2 *x32 = nullptr, *y32 = nullptr;
@@ -327,10 +329,10 @@ static void free_work(KrylovWork *w)
     delete w;
 }
 
-static h2_status get_work(h2_handle *h, int m, KrylovWork **out)
+static h2_status get_work(h2_handle *h, int m, bool flexible, KrylovWork **out)
 {
     KrylovWork *w = reinterpret_cast<KrylovWork *>(h->krylov);
-    if (w && w->m == m) {
+    if (w && w->m == m && w->flexible == flexible) {
         *out = w;
         return H2_OK;
     }
@@ -340,6 +342,7 @@ static h2_status get_work(h2_handle *h, int m, KrylovWork **out)
     const int n = h->n;
     w->n = n;
     w->m = m;
+    w->flexible = flexible;
     // rows per block: enough blocks to fill the GPU, at most 2048 rows each
     int nblk = std::max(1, std::min((n + KT - 1) / KT, 2 * 152 * 2));
     int rows = (n + nblk - 1) / nblk;
@@ -375,6 +378,7 @@ static h2_status get_work(h2_handle *h, int m, KrylovWork **out)
     const size_t otm = take(sizeof(double2) * n);
     const size_t ox = take(sizeof(float2) * n);
     const size_t oy = take(sizeof(float2) * n);
+    const size_t oz = flexible ? take(sizeof(double2) * (size_t)n * m) : 0;
     if (cudaMalloc(&w->block, off) != cudaSuccess || cudaMallocHost(&w->h_scal, 4 * sizeof(double)) != cudaSuccess) {
         free_work(w);
         set_error("h2_gmres: workspace allocation failed");
@@ -396,6 +400,7 @@ static h2_status get_work(h2_handle *h, int m, KrylovWork **out)
     w->tmp = reinterpret_cast<double2 *>(base + otm);
     w->x32 = reinterpret_cast<float2 *>(base + ox);
     w->y32 = reinterpret_cast<float2 *>(base + oy);
+    w->Z = flexible ? reinterpret_cast<double2 *>(base + oz) : nullptr;
     if (cudaMemset(K.ticket, 0, 4 * sizeof(unsigned)) != cudaSuccess) {
         free_work(w);
         return H2_ERR_CUDA;
@@ -462,11 +467,13 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
     const int m = opts->restart;
     if (m < 1 || m > 1024 || opts->maxit < 1 || !(opts->tol > 0.0))
         return (set_error("h2_gmres: need 1 <= restart <= 1024, maxit >= 1, tol > 0"), H2_ERR_ARG);
-    if (opts->precond != 0) return (set_error("h2_gmres: preconditioner not loaded"), H2_ERR_STATE);
+    const bool flexible = opts->precond != 0;
+    if (flexible && !h->precond)
+        return (set_error("h2_gmres: no preconditioner loaded (h2_set_preconditioner)"), H2_ERR_STATE);
     KCUDA(cudaSetDevice(h->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     KrylovWork *w = nullptr;
-    h2_status s = get_work(h, m, &w);
+    h2_status s = get_work(h, m, flexible, &w);
     if (s != H2_OK) return s;
     KrylovDev &K = w->K;
     const int n = h->n;
@@ -503,6 +510,7 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
         while (beta / bnorm > opts->tol && it < opts->maxit) {
             k_start<<<vb, 256, 0, st>>>(K, w->r, w->x32);
             KCUDA(cudaGetLastError());
+            if (flexible && (s = h2_apply_precond(h, K.V, w->Z, w->x32, st)) != H2_OK) return s;
             int j = 0, k = 0;
             for (j = 0; j < m && it < opts->maxit; ++j) {
                 if ((s = h2_matvec(h, w->x32, w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
@@ -523,11 +531,14 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
                 if (j + 1 < m) {
                     k_normalize<<<vb, 256, 0, st>>>(K, j + 1, w->x32);
                     KCUDA(cudaGetLastError());
+                    if (flexible && (s = h2_apply_precond(h, K.V + (size_t)(j + 1) * n, w->Z + (size_t)(j + 1) * n,
+                                                          w->x32, st)) != H2_OK)
+                        return s;
                 }
             }
             if (rs != H2_OK) break;
             k_backsolve<<<1, 32, 0, st>>>(K, k);
-            k_xupdate<<<vb, 256, sizeof(double2) * (m + 1), st>>>(K, k, x);
+            k_xupdate<<<vb, 256, sizeof(double2) * (m + 1), st>>>(K, flexible ? w->Z : K.V, k, x);
             KCUDA(cudaGetLastError());
             ++inf.restarts;
             if ((s = true_residual(h, w, b, x, false, opts->refine != 0, st)) != H2_OK) return s;

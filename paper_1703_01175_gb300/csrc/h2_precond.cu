@@ -1,0 +1,203 @@
+// The learned preconditioner held by a handle: a 3-D convolutional network
+// on the voxel grid (weights and grid map copied from the caller), applied
+// to one vector at a time inside flexible GMRES (h2_krylov.cu).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "h2_internal.h"
+#include "h2nn.h"
+
+namespace {
+
+struct Layer {
+    int ci, co, relu;
+    __nv_bfloat16 *w = nullptr;
+    float *b = nullptr;
+};
+
+struct PrecondState {
+    int Dx = 0, Dy = 0, Dz = 0;
+    int64_t V = 0;
+    int nv = 0;
+    int32_t *grid_of = nullptr;
+    float *aux = nullptr;
+    std::vector<Layer> layers;
+    __nv_bfloat16 *act[2] = {nullptr, nullptr};
+    float *out = nullptr;
+    double *scale = nullptr;  // [0] = sqrt(3 nv) / |v|, [1] = its inverse (set per application)
+};
+
+__global__ void set_scale_kernel(const double2 *__restrict__ v, int n, double *scale)
+{
+    // one block: |v| by a block reduction
+    double s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i].x * v[i].x + v[i].y * v[i].y;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        const double nrm = sqrt(t);
+        const double sc = nrm > 0 ? sqrt((double)n) / nrm : 1.0;
+        scale[0] = sc;
+        scale[1] = 1.0 / sc;
+    }
+}
+
+__global__ void c128_to_c64_kernel(const double2 *__restrict__ a, float2 *__restrict__ b, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+
+void free_state(PrecondState *P)
+{
+    if (!P) return;
+    cudaFree(P->grid_of);
+    cudaFree(P->aux);
+    for (auto &L : P->layers) {
+        cudaFree(L.w);
+        cudaFree(L.b);
+    }
+    cudaFree(P->act[0]);
+    cudaFree(P->act[1]);
+    cudaFree(P->out);
+    cudaFree(P->scale);
+    delete P;
+}
+
+}  // namespace
+
+void h2_free_precond(h2_handle *h)
+{
+    free_state(reinterpret_cast<PrecondState *>(h->precond));
+    h->precond = nullptr;
+}
+
+h2_status h2_apply_precond(h2_handle *h, const double2 *v, double2 *z, float2 *z32, cudaStream_t st)
+{
+    PrecondState *P = reinterpret_cast<PrecondState *>(h->precond);
+    if (!P) return H2_ERR_STATE;
+    const int n = 3 * P->nv;
+    set_scale_kernel<<<1, 1024, 0, st>>>(v, n, P->scale);
+    if (P->nv < P->V) {  // grid voxels that are not unknowns read as zero
+        if (cudaMemsetAsync(P->act[0], 0, (size_t)P->V * 8 * 2, st) != cudaSuccess) return H2_ERR_CUDA;
+    }
+    h2_status s = h2nn_pack(v, n, P->grid_of, P->aux, P->scale, P->act[0], 1, P->nv, P->V, st);
+    if (s != H2_OK) return s;
+    int cur = 0;
+    for (size_t li = 0; li < P->layers.size(); ++li) {
+        const Layer &L = P->layers[li];
+        const bool last = li + 1 == P->layers.size();
+        s = h2nn_conv3d_fwd(P->act[cur], L.w, L.b, last ? nullptr : P->act[1 - cur], last ? P->out : nullptr, 1,
+                            P->Dx, P->Dy, P->Dz, L.ci, L.co, L.relu, st);
+        if (s != H2_OK) return s;
+        cur = 1 - cur;
+    }
+    s = h2nn_unpack(P->out, P->layers.back().co, P->grid_of, P->scale + 1, z, n, 1, P->nv, P->V, st);
+    if (s != H2_OK) return s;
+    if (z32) {
+        c128_to_c64_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(z, z32, n);
+        if (cudaGetLastError() != cudaSuccess) return H2_ERR_CUDA;
+    }
+    return H2_OK;
+}
+
+extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy, int32_t Dz,
+                                           const int32_t *grid_of, const float *aux, int32_t n_layers,
+                                           const int32_t *layer_spec, const void *weights, const float *biases)
+{
+    if (!h) {
+        h2::set_error("h2_set_preconditioner: NULL handle");
+        return H2_ERR_ARG;
+    }
+    if (n_layers == 0) {  // remove
+        h2_free_precond(h);
+        return H2_OK;
+    }
+    const int64_t V = (int64_t)Dx * Dy * Dz;
+    if (Dx < 1 || Dy < 1 || Dz < 1 || n_layers < 1 || !grid_of || !layer_spec || !weights || !biases ||
+        h->n % 3 != 0 || V < h->n / 3) {
+        h2::set_error("h2_set_preconditioner: bad argument");
+        return H2_ERR_ARG;
+    }
+    const int nv = h->n / 3;
+    for (int p = 0; p < nv; ++p)
+        if (grid_of[p] < 0 || grid_of[p] >= V) {
+            h2::set_error("h2_set_preconditioner: grid index out of range");
+            return H2_ERR_ARG;
+        }
+    int prev = 8;
+    for (int l = 0; l < n_layers; ++l) {
+        const int ci = layer_spec[3 * l], co = layer_spec[3 * l + 1];
+        const bool ok = (ci == 8 || ci == 16 || ci == 32) && (co == 8 || co == 16 || co == 32) && ci == prev;
+        if (!ok) {
+            h2::set_error("h2_set_preconditioner: layer channels must chain 8 -> ... -> 8 in {8, 16, 32}");
+            return H2_ERR_ARG;
+        }
+        prev = co;
+    }
+    if (prev != 8) {
+        h2::set_error("h2_set_preconditioner: the last layer must have 8 output channels");
+        return H2_ERR_ARG;
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return H2_ERR_CUDA;
+    h2_free_precond(h);
+    auto *P = new PrecondState();
+    P->Dx = Dx;
+    P->Dy = Dy;
+    P->Dz = Dz;
+    P->V = V;
+    P->nv = nv;
+    auto fail = [&](const char *what) {
+        h2::set_error(std::string("h2_set_preconditioner: ") + what);
+        free_state(P);
+        return H2_ERR_ALLOC;
+    };
+    int cmax = 8;
+    const uint16_t *wsrc = reinterpret_cast<const uint16_t *>(weights);
+    const float *bsrc = biases;
+    for (int l = 0; l < n_layers; ++l) {
+        Layer L;
+        L.ci = layer_spec[3 * l];
+        L.co = layer_spec[3 * l + 1];
+        L.relu = layer_spec[3 * l + 2];
+        cmax = std::max(cmax, std::max(L.ci, L.co));
+        const size_t nw = (size_t)L.co * 27 * L.ci;
+        if (cudaMalloc(&L.w, nw * 2) != cudaSuccess || cudaMalloc(&L.b, L.co * sizeof(float)) != cudaSuccess) {
+            P->layers.push_back(L);
+            return fail("allocation failed");
+        }
+        cudaMemcpy(L.w, wsrc, nw * 2, cudaMemcpyHostToDevice);
+        cudaMemcpy(L.b, bsrc, L.co * sizeof(float), cudaMemcpyHostToDevice);
+        wsrc += nw;
+        bsrc += L.co;
+        P->layers.push_back(L);
+    }
+    if (cudaMalloc(&P->grid_of, nv * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&P->aux, V * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&P->act[0], V * cmax * 2) != cudaSuccess || cudaMalloc(&P->act[1], V * cmax * 2) != cudaSuccess ||
+        cudaMalloc(&P->out, V * 8 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&P->scale, 2 * sizeof(double)) != cudaSuccess)
+        return fail("allocation failed");
+    cudaMemcpy(P->grid_of, grid_of, nv * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (aux)
+        cudaMemcpy(P->aux, aux, V * sizeof(float), cudaMemcpyHostToDevice);
+    else
+        cudaMemset(P->aux, 0, V * sizeof(float));
+    // grid voxels that are not unknowns must read as zero input
+    cudaMemset(P->act[0], 0, V * cmax * 2);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        free_state(P);
+        h2::set_error("h2_set_preconditioner: upload failed");
+        return H2_ERR_CUDA;
+    }
+    h->precond = P;
+    return H2_OK;
+}

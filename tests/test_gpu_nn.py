@@ -1,0 +1,191 @@
+"""Kernels of the learned preconditioner against the FP64 oracle convolution.
+
+Bar: forward, data-gradient and weight-gradient convolutions within 1e-5 of
+the largest output entry of the oracle evaluated on the same bf16-rounded
+operands (FP32 accumulation of exact bf16 products); the chained network
+gradients against the oracle's chain rule; exact round trip of pack/unpack on
+bf16-representable inputs; Adam against its formula; flexible GMRES with an
+identity network reaching the oracle-checked tolerance; a short training run
+lowering the loss.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import cases
+import synth
+from oracle import conv, h2mv
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1703_01175_gb300 import build
+    build.build_all()
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16)
+
+
+def _rand(shape, seed, stream):
+    return (2.0 * synth.uniform(seed, int(np.prod(shape)), stream=stream) - 1.0).reshape(shape)
+
+
+SHAPES = [((5, 4, 3), 1, 8, 32), ((16, 8, 9), 2, 32, 32), ((7, 9, 4), 1, 32, 8), ((6, 5, 7), 2, 16, 16)]
+
+
+@pytest.mark.parametrize("dims,B,Cin,Cout", SHAPES)
+@pytest.mark.parametrize("relu", [0, 1])
+def test_conv_forward(dims, B, Cin, Cout, relu):
+    from paper_1703_01175_gb300 import precond as P
+    V = int(np.prod(dims))
+    x = _bf(_rand((B, V, Cin), 1, 0)).cuda()
+    w = _bf(_rand((Cout, 27, Cin), 1, 1) * 0.3).cuda()
+    bias = torch.from_numpy(_rand((Cout,), 1, 2).astype(np.float32)).cuda()
+    out = torch.empty((B, V, Cout), dtype=torch.float32, device="cuda")
+    outb = torch.empty((B, V, Cout), dtype=torch.bfloat16, device="cuda")
+    st = P._vp(torch.cuda.current_stream().cuda_stream)
+    P._call("h2nn_conv3d_fwd", P._p(x), P._p(w), P._p(bias), P._p(outb), P._p(out), B, *dims, Cin, Cout, relu, st)
+    ref = conv.conv3d_forward(x.float().cpu().numpy(), w.float().cpu().numpy(), bias.cpu().numpy(), B, dims,
+                              relu=bool(relu))
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+    assert np.abs(outb.float().cpu().numpy() - ref).max() <= 1e-2 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dims,B,Cin,Cout", SHAPES)
+def test_conv_gradients(dims, B, Cin, Cout):
+    from paper_1703_01175_gb300 import precond as P
+    V = int(np.prod(dims))
+    st = P._vp(torch.cuda.current_stream().cuda_stream)
+    x = _bf(_rand((B, V, Cin), 2, 0)).cuda()
+    w = _bf(_rand((Cout, 27, Cin), 2, 1) * 0.3).cuda()
+    dz = torch.from_numpy(_rand((B, V, Cout), 2, 2).astype(np.float32)).cuda()
+    dzb = dz.to(torch.bfloat16)
+    wt = torch.empty((Cin, 27, Cout), dtype=torch.bfloat16, device="cuda")
+    P._call("h2nn_flip_weights", P._p(w), P._p(wt), Cin, Cout, st)
+    dx = torch.empty((B, V, Cin), dtype=torch.float32, device="cuda")
+    P._call("h2nn_conv3d_fwd", P._p(dzb), P._p(wt), None, None, P._p(dx), B, *dims, Cout, Cin, 0, st)
+    ref_dx = conv.conv3d_backward_data(dzb.float().cpu().numpy(), w.float().cpu().numpy(), B, dims)
+    assert np.abs(dx.cpu().numpy() - ref_dx).max() <= 1e-5 * max(1.0, np.abs(ref_dx).max())
+    dw = torch.empty((Cout, 27, Cin), dtype=torch.float32, device="cuda")
+    db = torch.empty((Cout,), dtype=torch.float32, device="cuda")
+    P._call("h2nn_conv3d_bwd_weight", P._p(dz), P._p(x), P._p(dw), P._p(db), B, *dims, Cin, Cout, 0, st)
+    ref_dw, ref_db = conv.conv3d_backward_weight(dz.cpu().numpy(), x.float().cpu().numpy(), B, dims, Cin, Cout)
+    assert np.abs(dw.cpu().numpy() - ref_dw).max() <= 1e-5 * max(1.0, np.abs(ref_dw).max())
+    assert np.abs(db.cpu().numpy() - ref_db).max() <= 1e-5 * max(1.0, np.abs(ref_db).max())
+
+
+def test_network_gradients_against_oracle_chain():
+    """Two-layer ReLU network: every parameter gradient of the relative loss
+    against the oracle's chain rule on the same bf16 activations."""
+    from paper_1703_01175_gb300 import precond as P
+    dims, B = (6, 5, 4), 2
+    layers = [(8, 16, 1), (16, 8, 0)]
+    net = P.ConvNet(dims, B, layers=layers, seed=5)
+    V = net.V
+    x = _bf(_rand((B, V, 8), 3, 0)).cuda()
+    tgt = torch.from_numpy(_rand((B, V, 8), 3, 1).astype(np.float32)).cuda()
+    tgt[..., 6:] = 0
+    net.forward(x)
+    g = net.loss_and_grad(tgt)
+    gout = g.clone().cpu().numpy()
+    net.backward(g)
+    # oracle chain: the same bf16 activations the kernels used
+    a0 = net.acts[0].float().cpu().numpy()
+    a1 = net.acts[1].float().cpu().numpy()
+    W1 = net.Wb[1].float().cpu().numpy()
+    out = net.out.cpu().numpy()
+    t = tgt.cpu().numpy()
+    den = (t[..., :6] ** 2).sum(axis=(1, 2))
+    gref = np.zeros_like(out)
+    gref[..., :6] = 2 * (out[..., :6] - t[..., :6]) / (den[:, None, None] * B)
+    assert np.abs(gout - gref).max() <= 1e-5 * np.abs(gref).max()
+    dw1, db1 = conv.conv3d_backward_weight(gref, a1, B, dims, 16, 8)
+    assert np.abs(net.gW[1].cpu().numpy() - dw1).max() <= 1e-4 * np.abs(dw1).max()
+    assert np.abs(net.gb[1].cpu().numpy() - db1).max() <= 1e-4 * np.abs(db1).max()
+    g1 = conv.conv3d_backward_data(gref.astype(np.float32).astype(np.float64), W1, B, dims)
+    g1 = g1 * (a1 > 0)
+    dw0, db0 = conv.conv3d_backward_weight(g1, a0, B, dims, 8, 16)
+    # the data gradient passes through bf16 once (documented): compare at bf16 accuracy
+    assert np.abs(net.gW[0].cpu().numpy() - dw0).max() <= 1e-2 * np.abs(dw0).max()
+    assert np.abs(net.gb[0].cpu().numpy() - db0).max() <= 1e-2 * np.abs(db0).max()
+
+
+def test_adam_step_matches_formula():
+    from paper_1703_01175_gb300 import precond as P
+    n = 1000
+    p0 = _rand((n,), 4, 0).astype(np.float32)
+    g0 = _rand((n,), 4, 1).astype(np.float32)
+    p = torch.from_numpy(p0.copy()).cuda()
+    g = torch.from_numpy(g0).cuda()
+    m = torch.zeros(n, device="cuda")
+    v = torch.zeros(n, device="cuda")
+    st = P._vp(torch.cuda.current_stream().cuda_stream)
+    P._call("h2nn_adam", P._p(p), P._p(g), P._p(m), P._p(v), None, n, 1e-2, 0.9, 0.999, 1e-8, 1, st)
+    mh = (0.1 * g0) / (1 - 0.9)
+    vh = (0.001 * g0 * g0) / (1 - 0.999)
+    ref = p0 - 1e-2 * mh / (np.sqrt(vh) + 1e-8)
+    assert np.abs(p.cpu().numpy() - ref).max() <= 1e-6
+
+
+def test_pack_unpack_roundtrip():
+    from paper_1703_01175_gb300 import precond as P
+    c = cases.get("cube8")
+    dims = c.v.shape
+    gm = P.GridMap(dims, c.tree.perm, c.v.eps_r)
+    n = c.n
+    vals = _bf(_rand((2, n, 2), 5, 0)).float().numpy().astype(np.float64)
+    vec = torch.from_numpy(vals[..., 0] + 1j * vals[..., 1]).cuda()
+    scale = torch.tensor([1.0, 2.0], dtype=torch.float64, device="cuda")
+    chan = torch.zeros((2, gm.V, 8), dtype=torch.bfloat16, device="cuda")
+    st = P._vp(torch.cuda.current_stream().cuda_stream)
+    one = torch.ones(2, dtype=torch.float64, device="cuda")
+    gm.pack(vec, one, chan, st)
+    ch = chan.float().cpu().numpy()
+    # channel 6 holds chi of the voxel; component c of tree position p sits at grid voxel perm[p]
+    p, comp = 5, 2
+    v = c.tree.perm[p]
+    assert ch[1, v, 2 * comp] == vals[1, 3 * p + comp, 0] and ch[1, v, 2 * comp + 1] == vals[1, 3 * p + comp, 1]
+    assert abs(ch[0, v, 6] - (c.v.eps_r[v].real - 1)) < 1e-2
+    back = torch.zeros_like(vec)
+    gm.unpack(chan.float(), scale, back, st)
+    got = back.cpu().numpy()
+    assert np.array_equal(got[0], vec.cpu().numpy()[0])
+    assert np.array_equal(got[1], 2.0 * vec.cpu().numpy()[1])
+
+
+def test_fgmres_identity_network_and_training():
+    from paper_1703_01175_gb300 import h2 as h2py, precond as P
+    c = cases.get("cube8")
+    A = h2py.H2Matrix(c.arrays())
+    try:
+        gm = P.GridMap(c.v.shape, c.tree.perm, c.v.eps_r)
+        b = synth.default_rhs(synth.workload("cube8"))[c.tree.unknown_perm()]
+        bt = torch.from_numpy(b).cuda()
+        x0, info0 = A.gmres(bt, tol=1e-6, restart=30, refine=True)
+        layers, W, Bs = P.identity_layers()
+        P.load_into(A, layers, W, Bs, gm)
+        x1, info1 = A.gmres(bt, tol=1e-6, restart=30, refine=True, precond=1)
+        assert info1[0]["status"] == 0
+        res = np.linalg.norm(b - c.oracle_matvec(x1.cpu().numpy())) / np.linalg.norm(b)
+        assert res <= 1e-6
+        assert abs(info1[0]["iterations"] - info0[0]["iterations"]) <= 5
+        # short training on pairs from the method's own solves lowers the loss
+        rhs = [synth.random_plane_waves(c.v, 6, seed=5)[c.tree.unknown_perm(), j] for j in range(6)]
+        R, E = P.collect_pairs(A, gm, rhs, restart=5, tol=1e-7)
+        assert R is not None and R.shape[0] >= 12
+        net = P.ConvNet(c.v.shape, 4, seed=11)
+        hist = P.train(net, gm, R, E, epochs=12, lr=3e-3)
+        assert hist[-1] < 0.8 * hist[0]
+        P.load_net(A, net, gm)
+        x2, info2 = A.gmres(bt, tol=1e-6, restart=30, refine=True, precond=1)
+        assert info2[0]["status"] == 0
+        res2 = np.linalg.norm(b - c.oracle_matvec(x2.cpu().numpy())) / np.linalg.norm(b)
+        assert res2 <= 1e-6
+    finally:
+        A.close()

@@ -204,7 +204,10 @@ typedef struct {
     int32_t precond;   /* 0: none; 1: the handle's learned preconditioner as the
                           right preconditioner of flexible GMRES (Saad 1993):
                           z_j = M(v_j), A z_j enters the Arnoldi process and
-                          x += Z y at the end of each cycle */
+                          x += Z y at the end of each cycle. A cycle that
+                          reduces the true residual by less than 5% turns the
+                          preconditioner off for the rest of the solve (plain
+                          GMRES is the fallback). */
 } h2_solve_opts;
 
 /* Per right-hand-side outcome of h2_gmres. */
@@ -213,6 +216,7 @@ typedef struct {
     int32_t restarts;   /* completed cycles */
     double rel_res;     /* final true relative residual ||b - A x|| / ||b|| */
     int32_t status;     /* H2_OK, H2_ERR_NOT_CONVERGED or H2_ERR_BREAKDOWN */
+    int32_t precond_cycles; /* cycles run with the preconditioner (flexible GMRES) */
 } h2_solve_info;
 
 /*
@@ -241,7 +245,8 @@ h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t l
  * voxel's grid index. M(v): v is scaled to unit RMS and packed into 8
  * channels (Re, Im of the 3 components, aux[v] = a per-voxel input such as
  * chi, 0); the layers run in order (ReLU where layer_spec[3l+2] != 0); output
- * channels 0..5 are unpacked with the inverse scale.
+ * channels 0..5 are unpacked with the inverse scale and added to v: the
+ * network N models the correction beyond the identity, M(v) = v + N(v).
  * layer_spec: [3 n_layers] (Cin, Cout, relu), channels in {8, 16, 32}, first
  * Cin = 8, last Cout = 8. weights: bf16 (uint16) [Cout][27][Cin] per layer,
  * concatenated; biases: f32 [Cout] per layer, concatenated; aux: f32 [V] or

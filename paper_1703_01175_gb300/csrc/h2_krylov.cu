@@ -507,10 +507,12 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
         double beta = w->h_scal[0];
         int it = 0;
         h2_status rs = H2_OK;
+        bool pc = flexible;  // preconditioned cycles until one stagnates, then plain GMRES
         while (beta / bnorm > opts->tol && it < opts->maxit) {
+            const double beta_start = beta;
             k_start<<<vb, 256, 0, st>>>(K, w->r, w->x32);
             KCUDA(cudaGetLastError());
-            if (flexible && (s = h2_apply_precond(h, K.V, w->Z, w->x32, st)) != H2_OK) return s;
+            if (pc && (s = h2_apply_precond(h, K.V, w->Z, w->x32, st)) != H2_OK) return s;
             int j = 0, k = 0;
             for (j = 0; j < m && it < opts->maxit; ++j) {
                 if ((s = h2_matvec(h, w->x32, w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
@@ -531,16 +533,17 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
                 if (j + 1 < m) {
                     k_normalize<<<vb, 256, 0, st>>>(K, j + 1, w->x32);
                     KCUDA(cudaGetLastError());
-                    if (flexible && (s = h2_apply_precond(h, K.V + (size_t)(j + 1) * n, w->Z + (size_t)(j + 1) * n,
-                                                          w->x32, st)) != H2_OK)
+                    if (pc && (s = h2_apply_precond(h, K.V + (size_t)(j + 1) * n, w->Z + (size_t)(j + 1) * n,
+                                                    w->x32, st)) != H2_OK)
                         return s;
                 }
             }
             if (rs != H2_OK) break;
             k_backsolve<<<1, 32, 0, st>>>(K, k);
-            k_xupdate<<<vb, 256, sizeof(double2) * (m + 1), st>>>(K, flexible ? w->Z : K.V, k, x);
+            k_xupdate<<<vb, 256, sizeof(double2) * (m + 1), st>>>(K, pc ? w->Z : K.V, k, x);
             KCUDA(cudaGetLastError());
             ++inf.restarts;
+            if (pc) ++inf.precond_cycles;
             if ((s = true_residual(h, w, b, x, false, opts->refine != 0, st)) != H2_OK) return s;
             if ((s = read_scal(w, st)) != H2_OK) return s;
             beta = w->h_scal[0];
@@ -548,6 +551,7 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
                 rs = H2_ERR_BREAKDOWN;
                 break;
             }
+            if (pc && beta > 0.95 * beta_start) pc = false;  // stagnating: fall back to plain GMRES
         }
         inf.iterations = it;
         inf.rel_res = beta / bnorm;

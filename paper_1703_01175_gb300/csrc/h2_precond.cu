@@ -50,6 +50,15 @@ __global__ void set_scale_kernel(const double2 *__restrict__ v, int n, double *s
     }
 }
 
+// z += v (the network models the correction beyond the identity)
+__global__ void add_c128_kernel(double2 *__restrict__ z, const double2 *__restrict__ v, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        z[i].x += v[i].x;
+        z[i].y += v[i].y;
+    }
+}
+
 __global__ void c128_to_c64_kernel(const double2 *__restrict__ a, float2 *__restrict__ b, int n)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -102,6 +111,7 @@ h2_status h2_apply_precond(h2_handle *h, const double2 *v, double2 *z, float2 *z
     }
     s = h2nn_unpack(P->out, P->layers.back().co, P->grid_of, P->scale + 1, z, n, 1, P->nv, P->V, st);
     if (s != H2_OK) return s;
+    add_c128_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(z, v, n);
     if (z32) {
         c128_to_c64_kernel<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(z, z32, n);
         if (cudaGetLastError() != cudaSuccess) return H2_ERR_CUDA;

@@ -227,6 +227,27 @@ def collect_pairs(A, gm: GridMap, rhs_list, restart=10, tol=1e-6, maxit=4000):
     return torch.stack(R), torch.stack(E)
 
 
+def probe_pairs(A, count, seed=7, batch=32):
+    """Probe pairs through the method's own product: e random (real and
+    imaginary parts uniform in [-1, 1)), r = A e with the FP64-accumulated
+    product. They sample the inverse in every direction, whereas restart
+    residuals concentrate on the slowly converging modes."""
+    import torch
+    import synth
+    R, E = [], []
+    n = A.n
+    done = 0
+    while done < count:
+        k = min(batch, count - done)
+        e = torch.from_numpy(np.ascontiguousarray(synth.random_complex(n, seed, stream=300 + done // batch,
+                                                                       cols=k).T)).cuda()
+        for j in range(k):
+            R.append(A.matvec(e[j].contiguous(), prec="fp64acc"))
+            E.append(e[j].contiguous())
+        done += k
+    return torch.stack(R), torch.stack(E)
+
+
 def train(net: ConvNet, gm: GridMap, R, E, epochs=20, lr=2e-3, seed=3, log=None):
     """Fit net(r_hat) ~ e_hat - r_hat with r_hat = s r, e_hat = s e,
     s = sqrt(n)/|r| per pair: the network learns the correction beyond the
@@ -292,3 +313,95 @@ def identity_layers():
     """A one-layer network with zero output: M(v) = v + 0."""
     w = np.zeros((8, 27, 8), dtype=np.float32)
     return [(8, 8, 0)], [w], [np.zeros(8, dtype=np.float32)]
+
+
+def transpose_arrays(a):
+    """H^2 arrays of A^T from those of A = near + sum U^t S^{t,s} W^{sT}:
+    row and column bases exchange (U <-> W), couplings and near blocks are
+    transposed and move to the mirrored block position (the partition is
+    symmetric)."""
+    nc = len(a.size)
+
+    def blk(flat, off, r, c):
+        return np.asarray(flat[off:off + r * c]).reshape(c, r).T
+
+    leaves = [t for t in range(nc) if a.child[2 * t] < 0]
+    parent = np.full(nc, -1)
+    for t in range(nc):
+        if a.child[2 * t] >= 0:
+            parent[a.child[2 * t]] = t
+            parent[a.child[2 * t + 1]] = t
+    rank, size = a.rank, a.size
+    U = {t: blk(a.U, a.U_off[t], size[t], rank[t]) for t in leaves}
+    W = U if a.W is None else {t: blk(a.W, a.W_off[t], size[t], rank[t]) for t in leaves}
+    T = {t: blk(a.T, a.T_off[t], rank[t], rank[parent[t]]) for t in range(1, nc) if rank[t] and rank[parent[t]]}
+    S, Z = {}, {}
+    for t in range(nc):
+        for j in range(a.adm_ptr[t], a.adm_ptr[t + 1]):
+            s = int(a.adm_col[j])
+            S[(s, t)] = blk(a.S, a.S_off[j], rank[t], rank[s]).T
+        for j in range(a.near_ptr[t], a.near_ptr[t + 1]):
+            s = int(a.near_col[j])
+            Z[(s, t)] = blk(a.Z, a.Z_off[j], size[t], size[s]).T
+    return h2py.arrays_from_blocks(a.n, a.level_ptr, a.child, a.begin, a.size, a.rank, W, U, T, S, Z,
+                                   dtype=a.U.dtype)
+
+
+def train_residual(net: ConvNet, gm: GridMap, A, At, R, epochs=20, lr=2e-3, seed=3, log=None):
+    """Fit the preconditioner in residual space: minimise, over the training
+    residuals r, ||A M(r) - r||^2 / ||r||^2 with M(r) = r + N(s r) / s,
+    s = sqrt(n) / ||r|| (right approximate inverse). The gradient with respect
+    to M(r) is 2 A^H (A M(r) - r) / ||r||^2, formed with the transposed
+    operator At: A^H y = conj(At conj(y)). Products are batched FP32 H^2
+    products; the network runs on the library's convolution kernels."""
+    import torch
+    import synth
+    P_, n = R.shape
+    st = net.stream()
+    B = net.B
+    rnorm = torch.linalg.vector_norm(R, dim=1)
+    scale = (math.sqrt(n) / rnorm).to(torch.float64).contiguous()
+    inv_scale = (1.0 / scale).contiguous()
+    Xb = torch.empty((B, net.V, 8), dtype=torch.bfloat16, device=net.dev)
+    Z = torch.empty((B, n), dtype=torch.complex128, device=net.dev)
+    Gb = torch.empty((B, net.V, 8), dtype=torch.bfloat16, device=net.dev)
+    steps_per_epoch = max(1, P_ // B)
+    total = epochs * steps_per_epoch
+    step = 0
+    history = []
+    for ep in range(epochs):
+        order = np.argsort(synth.uniform(seed, P_, stream=400 + ep))
+        ep_loss = []
+        for sidx in range(steps_per_epoch):
+            idx = torch.as_tensor(order[sidx * B:(sidx + 1) * B], device=net.dev)
+            if len(idx) < B:
+                break
+            r = R[idx].contiguous()
+            sc, isc = scale[idx].contiguous(), inv_scale[idx].contiguous()
+            gm.pack(r, sc, Xb, st)
+            out = net.forward(Xb)
+            gm.unpack(out, isc, Z, st)            # Z = N(s r) / s
+            Z += r                                 # M(r)
+            Zc = Z.to(torch.complex64).T.contiguous().T          # (n, B) column-major
+            AZ = A.matvec(Zc).to(torch.complex128)               # (n, B)
+            D = AZ - r.T                                          # residual of the preconditioned map
+            rn2 = (rnorm[idx] ** 2)
+            loss = (torch.linalg.vector_norm(D, dim=0) ** 2 / rn2).mean()
+            Dc = D.conj().to(torch.complex64).contiguous()       # conj(D), column-major view (n, B)
+            G = At.matvec(Dc.T.contiguous().T).to(torch.complex128).conj()   # A^H D
+            G = G * (2.0 / (rn2 * B))                             # d loss / d M(r), per column
+            # d loss / d out = (d loss / d Z) / s ; pack expects rows per sample
+            gm.pack(G.T.contiguous(), isc, Gb, st)
+            g = net.g1.reshape(-1)[:B * net.V * 8].view(B, net.V, 8)
+            g.copy_(Gb.float())
+            g[..., 6:] = 0.0
+            net.backward(g)
+            cur_lr = lr * 0.5 * (1 + math.cos(math.pi * step / total))
+            net.adam(cur_lr)
+            ep_loss.append(loss)
+            step += 1
+        mean_loss = float(torch.stack(ep_loss).mean()) if ep_loss else float("nan")
+        history.append(mean_loss)
+        if log:
+            log(f"epoch {ep}: residual-space loss {mean_loss:.4f}")
+    return history

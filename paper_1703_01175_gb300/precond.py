@@ -382,13 +382,13 @@ def train_residual(net: ConvNet, gm: GridMap, A, At, R, epochs=20, lr=2e-3, seed
             out = net.forward(Xb)
             gm.unpack(out, isc, Z, st)            # Z = N(s r) / s
             Z += r                                 # M(r)
-            Zc = Z.to(torch.complex64).T.contiguous().T          # (n, B) column-major
+            Zc = Z.to(torch.complex64).contiguous().T            # (n, B) column-major view
             AZ = A.matvec(Zc).to(torch.complex128)               # (n, B)
             D = AZ - r.T                                          # residual of the preconditioned map
             rn2 = (rnorm[idx] ** 2)
             loss = (torch.linalg.vector_norm(D, dim=0) ** 2 / rn2).mean()
-            Dc = D.conj().to(torch.complex64).contiguous()       # conj(D), column-major view (n, B)
-            G = At.matvec(Dc.T.contiguous().T).to(torch.complex128).conj()   # A^H D
+            Dc = D.conj().to(torch.complex64).T.contiguous().T   # conj(D), (n, B) column-major
+            G = At.matvec(Dc).to(torch.complex128).conj()         # A^H D
             G = G * (2.0 / (rn2 * B))                             # d loss / d M(r), per column
             # d loss / d out = (d loss / d Z) / s ; pack expects rows per sample
             gm.pack(G.T.contiguous(), isc, Gb, st)

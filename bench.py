@@ -291,6 +291,38 @@ def run_ours(args, rank, world, local_rank):
         mr["speedup_vs_single_rhs_fp32"] = (ms * R) / mr["splitbf16"]["ms"]
         mr["tc_entries"] = tc_entries
 
+    # "new" solve: R right-hand sides in lockstep, split-bf16 tensor-core products, FP64 CGS2 Arnoldi,
+    # FP64-accumulated restart residuals; compared per right-hand side with plain single-RHS GMRES
+    if args.gmres_batch > 0:
+        R = args.gmres_batch
+        Bm = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
+        Bt = torch.from_numpy(np.asfortranarray(Bm)).to(dev).t().contiguous().t()
+        m_new = args.gmres_restart
+        for label, rst in (("plain_m%d" % m_new, m_new),):
+            torch.cuda.synchronize(dev)
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            xs, info = A.gmres(Bt[:, 0].contiguous(), tol=w.tol, restart=rst, maxit=4000, refine=True)
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            gm[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
+                         "rel_res": info[0]["rel_res"], "status": info[0]["status"]}
+        torch.cuda.synchronize(dev)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Xs, info = A.gmres_batched(Bt, tol=w.tol, restart=m_new, maxit=4000, refine=True, prec="splitbf16")
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_new = g0.elapsed_time(g1)
+        gm["new_batched"] = {"nrhs": R, "restart": m_new, "ms_total": t_new, "ms_per_rhs": t_new / R,
+                             "converged": sum(1 for i in info if i["status"] == 0),
+                             "max_rel_res": max(i["rel_res"] for i in info),
+                             "mean_iterations": float(np.mean([i["iterations"] for i in info])),
+                             "products": "split-bf16 tensor cores, FP64 CGS2, FP64-accumulated restart residuals"}
+        gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
+
     # end to end through the host-pointer entry point
     for _ in range(2):
         A.matvec_host(x_np)
@@ -353,6 +385,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gmres-batch", type=int, default=16, help="right-hand sides of the batched solve (0: skip)")
+    ap.add_argument("--gmres-restart", type=int, default=400, help="restart of the batched / plain comparison")
     ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")
     ap.add_argument("--only-mrhs", action="store_true",

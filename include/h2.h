@@ -238,6 +238,23 @@ h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t l
                    const h2_solve_opts *opts, h2_solve_info *info, void *stream);
 
 /*
+ * Batched restarted GMRES(m): the nrhs right-hand sides advance in lockstep,
+ * each with its own Krylov basis, Hessenberg matrix and Givens rotations, so
+ * every Arnoldi step runs ONE multi-RHS product (prec = H2_PREC_FP32: CUDA-core
+ * complex GEMMs; H2_PREC_SPLITBF16: tensor cores) and the FP64 Gram-Schmidt
+ * (CGS2), rotation and back-substitution kernels are batched over the
+ * right-hand sides. A right-hand side whose residual estimate drops below
+ * tol / 2 stops contributing at the end of the cycle. Restart residuals:
+ * FP64-accumulated products when opts->refine (one per right-hand side),
+ * else one batched product with `prec`. opts->precond must be 0.
+ * b, x: device c128, nrhs columns with leading dimension ld >= N.
+ * Workspace: N x (m+1) x nrhs c128 basis plus O(N nrhs) vectors, allocated
+ * on first use and kept by the handle. Synchronises `stream` once per step.
+ */
+h2_status h2_gmres_batched(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld,
+                           const h2_solve_opts *opts, h2_prec prec, h2_solve_info *info, void *stream);
+
+/*
  * Load (or, with n_layers = 0, remove) the learned preconditioner used by
  * h2_gmres with precond = 1: a chain of 3x3x3 convolutions on the
  * Dx x Dy x Dz voxel grid (include/h2nn.h). Unknown 3 p + c of the operator is

@@ -95,6 +95,10 @@ def lib() -> ctypes.CDLL:
     L.h2_gmres.restype = ctypes.c_int
     L.h2_gmres.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                            ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
+    L.h2_gmres_batched.restype = ctypes.c_int
+    L.h2_gmres_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_int64, ctypes.POINTER(_SolveOpts), ctypes.c_int,
+                                   ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
     L.h2_device_status.restype = ctypes.c_int
     L.h2_device_status.argtypes = [ctypes.c_void_p]
     L.h2_status_string.restype = ctypes.c_char_p
@@ -114,7 +118,8 @@ def _check(status: int, where: str):
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
     return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
-            "h2_profile_matvec", "h2_gmres", "h2_device_status", "h2_status_string", "h2_last_error"]
+            "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_status_string",
+            "h2_last_error"]
 
 
 # ---------------------------------------------------------------------------
@@ -294,6 +299,26 @@ class H2Matrix:
         _check(lib().h2_matvec_host(self._h, xf.ctypes.data, y.ctypes.data, nrhs, self.n, PREC[prec]),
                "h2_matvec_host")
         return y
+
+    def gmres_batched(self, B, X=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
+                      prec="splitbf16", stream=None, check=True):
+        """Batched GMRES for B (n, nrhs) column-major complex128 on the device."""
+        import torch
+        if B.dtype != torch.complex128 or not B.is_cuda:
+            raise TypeError("B must be a CUDA complex128 tensor")
+        nrhs, ld = self._shape(B)
+        if X is None:
+            X = torch.zeros_like(B)
+        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), 0)
+        infos = (_SolveInfo * nrhs)()
+        st = torch.cuda.current_stream(B.device).cuda_stream if stream is None else stream
+        status = lib().h2_gmres_batched(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), nrhs,
+                                        ld, ctypes.byref(opts), PREC[prec], infos, ctypes.c_void_p(st))
+        out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status}
+               for i in infos]
+        if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
+            _check(status, "h2_gmres_batched")
+        return X, out
 
     def device_status(self) -> int:
         """Synchronise and return H2_OK or H2_ERR_TIMEOUT (a bounded wait ran out)."""

@@ -178,6 +178,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w, arrs, perm, t_build = build_workload(args.workload)
     A = h2py.H2Matrix(arrs, device=local_rank)
+    tuning = A.autotune()
     st = A.stats()
     n = arrs.n
     x_np = synth.random_complex(n, 1).astype(np.complex64)
@@ -359,6 +360,7 @@ def run_ours(args, rank, world, local_rank):
                    "adm_blocks": st["adm_blocks"], "max_rank": st["max_rank"]},
         "matvec_gbs": mv_gbs, "matvec_frac_hbm": mv_gbs / hbm,
         "stages_ms": prof,
+        "autotune": {k: v["threads"] for k, v in tuning.items()},
         "gmres": gm,
         "mrhs": mr,
         "roofline": ({"bound": "hbm", "kernel": "rowgemv (coupling launch, all levels)", "achieved": couple_gbs,

@@ -105,8 +105,11 @@ typedef struct {
  * admissible and near blocks tile the N x N index square exactly once.
  * The upload is synchronous. On success *out receives a new handle; on
  * failure *out is set to NULL and nothing is leaked.
- * `opts` may be NULL or a string of "key=value" pairs separated by ';'
- * (currently: "device=<int>").
+ * `opts` may be NULL or a string of "key=value" pairs separated by ';':
+ * "device=<int>" (default 0), "graphs=0|1" (default 1: the single-RHS FP32
+ * product is captured into a CUDA graph per (x, y) pair on first use and
+ * replayed afterwards; at most 8 graphs are kept, least recently used first
+ * out).
  */
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);
@@ -143,6 +146,15 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host,
    inside a tensor-core kernel ran out since the handle was loaded (the
    kernel then skipped its output), else H2_OK. */
 h2_status h2_device_status(h2_handle *h);
+
+/*
+ * Autotune the launch shape of every stage of the FP32 product: for each
+ * block-row phase, time each admissible CTA size (128 ... 1024 threads) with
+ * CUDA events and keep the fastest. Writes a JSON report (phase -> chosen
+ * threads, time in microseconds, all candidates) into report[0..report_len)
+ * when report is not NULL. Synchronous; drops cached graphs.
+ */
+h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len);
 
 /* Sizes of the loaded representation (all counts in complex elements). */
 typedef struct {

@@ -242,6 +242,9 @@ void h2_free(h2_handle *h)
     cudaFree(h->d_coefm);
     cudaFree(h->d_xbuf);
     cudaFree(h->d_ybuf);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    if (h->s_cap) cudaStreamDestroy(h->s_cap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_near) cudaEventDestroy(h->ev_near);
     if (h->s_aux) cudaStreamDestroy(h->s_aux);
@@ -260,13 +263,17 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     if (st != H2_OK) return st;
 
     int device = 0;
+    bool use_graphs = true;
     if (opts) {
         const char *p = strstr(opts, "device=");
         if (p) device = atoi(p + 7);
+        const char *g = strstr(opts, "graphs=");
+        if (g) use_graphs = atoi(g + 7) != 0;
     }
     h2_handle *h = new (std::nothrow) h2_handle();
     if (!h) return H2_ERR_ALLOC;
     h->device = device;
+    h->use_graphs = use_graphs;
     const int32_t n = tree->n, nc = tree->n_clusters, nl = tree->n_levels;
     h->n = n;
     h->nc = nc;
@@ -500,6 +507,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         H2_LOAD_CUDA(cudaMemcpy(h->d_tasks, htasks.data(), htasks.size() * sizeof(Task), cudaMemcpyHostToDevice));
     H2_LOAD_CUDA(cudaMalloc(&h->d_coef, std::max<int64_t>(1, 2 * ktot) * sizeof(double2)));
     H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking));
+    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking));
     H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming));
 
@@ -606,6 +614,52 @@ static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st)
     return H2_OK;
 }
 
+// The single-RHS FP32 product as one CUDA graph launch: captured once per
+// (x, y) pair on an internal stream (the fork to the near-field stream and the
+// join are captured as graph edges) and replayed on the caller's stream.
+static h2_status run_single_graph(h2_handle *h, const float2 *x, float2 *y, cudaStream_t st)
+{
+    for (auto &g : h->graphs)
+        if (g.x == x && g.y == y) {
+            g.last_use = ++h->graph_clock;
+            H2_CUDA(cudaGraphLaunch(g.exec, st));
+            return H2_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    H2_CUDA(cudaStreamBeginCapture(h->s_cap, cudaStreamCaptureModeThreadLocal));
+    h2_status s = run_single<float2>(h, x, y, h->s_cap);
+    const cudaError_t ec = cudaStreamEndCapture(h->s_cap, &graph);
+    if (s != H2_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        h->use_graphs = false;  // capture unsupported here: direct launches from now on
+        return run_single<float2>(h, x, y, st);
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        h->use_graphs = false;
+        return run_single<float2>(h, x, y, st);
+    }
+    if (h->graphs.size() >= 8) {
+        auto victim = std::min_element(h->graphs.begin(), h->graphs.end(),
+                                       [](const auto &a, const auto &b) { return a.last_use < b.last_use; });
+        cudaGraphExecDestroy(victim->exec);
+        h->graphs.erase(victim);
+    }
+    h->graphs.push_back({x, y, exec, ++h->graph_clock});
+    H2_CUDA(cudaGraphLaunch(exec, st));
+    return H2_OK;
+}
+
+static void drop_graphs(h2_handle *h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
 extern "C" {
 
 h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t ld, h2_prec prec,
@@ -624,6 +678,8 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
                                   reinterpret_cast<float2 *>(y), nrhs > 1 ? ld : h->n, nrhs, st);
     if (nrhs > 1 && prec == H2_PREC_FP32)
         return h2_run_multi_f32(h, reinterpret_cast<const float2 *>(x), ld, reinterpret_cast<float2 *>(y), ld, nrhs, st);
+    if (nrhs == 1 && prec == H2_PREC_FP32 && h->use_graphs)
+        return run_single_graph(h, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), st);
     for (int32_t r = 0; r < nrhs; ++r) {
         h2_status s;
         if (prec == H2_PREC_FP32)
@@ -720,3 +776,80 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
 }
 
 }  // extern "C"
+
+// ---- autotuner -----------------------------------------------------------------------
+// For every phase, time the block-row GEMV launch with each admissible CTA
+// size (CUDA events, median of 3 after a warm-up) and keep the fastest. The
+// report is a JSON object {phase: {"threads": T, "us": t, "tried": {T: t}}}.
+extern "C" h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len)
+{
+    if (!h) return arg_error("h2_autotune: NULL handle");
+    H2_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->s_aux;
+    float2 *xb = nullptr, *yb = nullptr;
+    if (cudaMalloc(&xb, sizeof(float2) * h->n) != cudaSuccess || cudaMalloc(&yb, sizeof(float2) * h->n) != cudaSuccess) {
+        cudaFree(xb);
+        set_error("h2_autotune: allocation failed");
+        return H2_ERR_ALLOC;
+    }
+    H2_CUDA(cudaMemsetAsync(xb, 0, sizeof(float2) * h->n, st));
+    float2 *coef = reinterpret_cast<float2 *>(h->d_coef);
+    H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * 2 * std::max<int64_t>(1, h->ktot), st));
+    cudaEvent_t e0, e1;
+    H2_CUDA(cudaEventCreate(&e0));
+    H2_CUDA(cudaEventCreate(&e1));
+    std::string js = "{";
+    bool first = true;
+    auto tune = [&](Phase &ph, const std::string &name, bool to_y) -> h2_status {
+        if (ph.ntask() == 0) return H2_OK;
+        int maxP = 1;
+        for (const Task &t : ph.tasks) maxP = std::max(maxP, t.mpad / 2);
+        static const int cand[] = {128, 192, 256, 384, 512, 768, 1024};
+        int best = ph.threads;
+        float best_us = 1e30f;
+        std::string tried;
+        for (int T : cand) {
+            if (T < maxP) continue;
+            ph.threads = T;
+            float ts[3];
+            for (int rep = 0; rep < 4; ++rep) {
+                H2_CUDA(cudaEventRecord(e0, st));
+                H2_CUDA(launch_phase_f32(ph, h->d_mat, h->d_segs, xb, coef, to_y ? yb : coef, 0, st));
+                H2_CUDA(cudaEventRecord(e1, st));
+                H2_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) ts[rep - 1] = ms;
+            }
+            std::sort(ts, ts + 3);
+            const float us = ts[1] * 1e3f;
+            tried += (tried.empty() ? "" : ", ") + std::string("\"") + std::to_string(T) + "\": " + std::to_string(us);
+            if (us < best_us) {
+                best_us = us;
+                best = T;
+            }
+        }
+        ph.threads = best;
+        js += (first ? "" : ", ") + std::string("\"") + name + "\": {\"threads\": " + std::to_string(best) +
+              ", \"us\": " + std::to_string(best_us) + ", \"tried\": {" + tried + "}}";
+        first = false;
+        return H2_OK;
+    };
+    h2_status s = H2_OK;
+    if ((s = tune(h->near, "near", true)) == H2_OK && (s = tune(h->couple, "couple", false)) == H2_OK &&
+        (s = tune(h->upleaf, "upleaf", false)) == H2_OK && (s = tune(h->leafexp, "leafexp", true)) == H2_OK) {
+        for (int l = 0; l < h->nlev && s == H2_OK; ++l) s = tune(h->up[l], "up" + std::to_string(l), false);
+        for (int l = 0; l < h->nlev && s == H2_OK; ++l) s = tune(h->down[l], "down" + std::to_string(l), false);
+    }
+    js += "}";
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(xb);
+    cudaFree(yb);
+    drop_graphs(h);  // launch shapes changed: re-capture
+    if (report && report_len > 0) {
+        strncpy(report, js.c_str(), (size_t)report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return s;
+}

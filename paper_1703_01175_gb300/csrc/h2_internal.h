@@ -118,6 +118,17 @@ struct h2_handle {
     std::vector<h2::Seg> segs_host;   // host copy of the input segments (split-bf16 packing)
     void *precond = nullptr;          // learned preconditioner (h2_precond.cu)
     void *bkrylov = nullptr;          // batched GMRES workspace (h2_bkrylov.cu)
+    // captured single-RHS FP32 products, one per (x, y) pair (h2_api.cu)
+    struct GraphEntry {
+        const void *x;
+        void *y;
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    bool use_graphs = true;
+    cudaStream_t s_cap = nullptr;
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
 };
 

@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
     L.h2_gmres_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_int64, ctypes.POINTER(_SolveOpts), ctypes.c_int,
                                    ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
+    L.h2_autotune.restype = ctypes.c_int
+    L.h2_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
     L.h2_device_status.restype = ctypes.c_int
     L.h2_device_status.argtypes = [ctypes.c_void_p]
     L.h2_status_string.restype = ctypes.c_char_p
@@ -118,8 +120,8 @@ def _check(status: int, where: str):
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
     return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
-            "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_status_string",
-            "h2_last_error"]
+            "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_autotune",
+            "h2_status_string", "h2_last_error"]
 
 
 # ---------------------------------------------------------------------------
@@ -208,7 +210,7 @@ def _ip(a, t):
 class H2Matrix:
     """A loaded H^2 operator on one GPU (wraps an h2_handle)."""
 
-    def __init__(self, arrs: H2Arrays, device: int = 0):
+    def __init__(self, arrs: H2Arrays, device: int = 0, graphs: bool = True):
         L = lib()
         cplx = arrs.U.dtype
         if cplx not in (np.complex64, np.complex128):
@@ -233,7 +235,7 @@ class H2Matrix:
                   _ip(arrs.near_ptr, _i32p), _ip(arrs.near_col, _i32p),
                   arrs.Z.ctypes.data, _ip(arrs.Z_off, _i64p), arrs.Z.size)
         h = ctypes.c_void_p()
-        _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), f"device={device}".encode(),
+        _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), f"device={device};graphs={int(graphs)}".encode(),
                          ctypes.byref(h)), "h2_load")
         self._h = h
         self.device = device
@@ -319,6 +321,13 @@ class H2Matrix:
         if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
             _check(status, "h2_gmres_batched")
         return X, out
+
+    def autotune(self) -> dict:
+        """Pick the fastest CTA size of every product stage (returns the report)."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(lib().h2_autotune(self._h, buf, len(buf)), "h2_autotune")
+        return json.loads(buf.value.decode())
 
     def device_status(self) -> int:
         """Synchronise and return H2_OK or H2_ERR_TIMEOUT (a bounded wait ran out)."""

@@ -134,3 +134,25 @@ def test_splitbf16_tensor_cores_match_oracle(loaded, name, R):
         assert _rel(Y, Y_or) <= 1e-4
         colerr = np.linalg.norm(Y - Y_or, axis=0) / np.linalg.norm(Y_or, axis=0)
         assert colerr.max() <= 1e-4
+
+
+def test_graph_replay_and_autotune(loaded):
+    """The captured-graph product equals the directly launched one bitwise;
+    after autotuning the launch shapes the product still matches the oracle."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube12")
+    A = _mat(loaded, "cube12")
+    B = h2.H2Matrix(c.arrays(), graphs=False)
+    try:
+        x = torch.from_numpy(synth.random_complex(c.n, 23).astype(np.complex64)).cuda()
+        y1 = A.matvec(x).clone()
+        y2 = A.matvec(x).clone()          # replay of the captured graph
+        y3 = B.matvec(x)
+        assert torch.equal(y1, y2) and torch.equal(y1, y3)
+        rep = A.autotune()
+        assert "near" in rep and rep["near"]["threads"] in (128, 192, 256, 384, 512, 768, 1024)
+        y4 = A.matvec(x).cpu().numpy()
+        y_or = c.oracle_matvec(x.cpu().numpy().astype(np.complex128))
+        assert _rel(y4, y_or) <= 1e-5
+    finally:
+        B.close()

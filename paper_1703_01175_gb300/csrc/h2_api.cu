@@ -263,17 +263,20 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     if (st != H2_OK) return st;
 
     int device = 0;
-    bool use_graphs = true;
+    bool use_graphs = true, tc_pipeline = true;
     if (opts) {
         const char *p = strstr(opts, "device=");
         if (p) device = atoi(p + 7);
         const char *g = strstr(opts, "graphs=");
         if (g) use_graphs = atoi(g + 7) != 0;
+        const char *tp = strstr(opts, "tc_pipeline=");
+        if (tp) tc_pipeline = atoi(tp + 12) != 0;
     }
     h2_handle *h = new (std::nothrow) h2_handle();
     if (!h) return H2_ERR_ALLOC;
     h->device = device;
     h->use_graphs = use_graphs;
+    h->tc_pipeline = tc_pipeline;
     const int32_t n = tree->n, nc = tree->n_clusters, nl = tree->n_levels;
     h->n = n;
     h->nc = nc;

@@ -70,6 +70,7 @@ struct UPhase {
     int32_t *d_chunks = nullptr;
     uint8_t *d_images = nullptr;
     int64_t image_bytes = 0;
+    int nmax = 16;                // largest MMA N of the phase's tiles
 };
 
 struct SplitState {
@@ -80,6 +81,7 @@ struct SplitState {
     void *xhi = nullptr, *xlo = nullptr, *chi = nullptr, *clo = nullptr;  // bf16 planes
     int rcap = 0;
     int *d_err = nullptr;         // set when a bounded wait ran out
+    bool pipeline = true;         // warp-specialised multi-stage kernel (else the two-stage one)
 };
 
 void set_error(const std::string &msg);
@@ -128,6 +130,7 @@ struct h2_handle {
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
     bool use_graphs = true;
+    bool tc_pipeline = true;          // split-bf16: warp-specialised multi-stage tensor-core kernel
     cudaStream_t s_cap = nullptr;
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
 };
@@ -138,6 +141,7 @@ void h2_free_split(h2_handle *h);
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st);
 h2_status h2_split_error_flag(h2_handle *h, int *flag);
+h2_status h2_split_set_pipeline(h2_handle *h, int on);
 void h2_free_precond(h2_handle *h);
 void h2_free_bkrylov(h2_handle *h);
 // z = M(v) for one c128 vector (v of unit norm or any norm); also writes c64 z32 when not NULL

@@ -87,6 +87,18 @@ __device__ __forceinline__ void cp16(void *dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// 16-byte cp.async that reads src_bytes (0 or 16) and zero-fills the rest
+__device__ __forceinline__ void cp16z(void *dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 {
@@ -262,6 +274,157 @@ umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ ch
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// Warp-specialised, NS-stage pipelined version of umma_task_kernel.
+// Warps 0-2 produce: for each K stage they wait until its buffer is free
+// (tcgen05.commit of the MMAs that read it), issue the bulk copy of the matrix
+// image (thread 0, with expect_tx) and gather the right-hand-side chunks with
+// cp.async (zero-filled where there is no source), wait for their own copies,
+// fence them to the async proxy and arrive on the stage's `full` barrier
+// (96 arrivals + the expect_tx arrival). Warp 3 (one lane) issues the MMAs of a
+// stage once it is full and commits them to the stage's `empty` barrier. All
+// four warps then read the accumulator out of tensor memory.
+template <int NS>
+__global__ void __launch_bounds__(UT, 1)
+umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
+               const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
+               const __nv_bfloat16 *__restrict__ xlo, int64_t ldp, int nrhs, float2 *__restrict__ out,
+               int64_t ldo, int beta_one, int nmax, int *__restrict__ err)
+{
+    constexpr int NPROD = 96;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const UTask tk = tasks[blockIdx.x];
+    const int N = tk.n;
+    const uint32_t abytes = (uint32_t)N * 128u;
+    const uint32_t astride = 2u * (uint32_t)nmax * 128u;
+    uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
+    uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + NS;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.y * MT;
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], NPROD + 1);
+            mbar_init(&empty[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 3) {
+        const int pt = tid;  // 0..95
+        for (int s = 0; s < tk.nst; ++s) {
+            const int b = s % NS;
+            if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1)) {
+                abort_flag = 1;
+                break;
+            }
+            uint8_t *sx = sxb + b * 2 * XPLANE;
+            uint8_t *sa = sab + b * astride;
+            if (pt == 0) {
+                mbar_expect_tx(&full[b], 2 * abytes);
+                bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
+            }
+            const int32_t *ch = chunks + tk.chunk_off + (int64_t)s * (CPS / 4);
+            for (int e = pt; e < 2 * MT * 8; e += NPROD) {
+                const int plane = e >= MT * 8;
+                const int ee = e - plane * MT * 8;
+                const int r = ee >> 3, q = ee & 7;
+                uint8_t *dst = sx + plane * XPLANE + r * 128 + ((q ^ (r & 7)) << 4);
+                const int32_t ci = ch[q];
+                const int rr = r0 + r;
+                const __nv_bfloat16 *pl = plane ? xlo : xhi;
+                const bool ok = ci >= 0 && rr < nrhs;
+                const __nv_bfloat16 *src = ok ? pl + (int64_t)rr * ldp + 2 * (int64_t)ci : pl;
+                cp16z(dst, src, ok ? 16u : 0u);
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full[b]);
+        }
+    } else if (lane == 0) {
+        const uint32_t idesc = idesc_bf16(N);
+        for (int s = 0; s < tk.nst; ++s) {
+            const int b = s % NS;
+            if (!mbar_wait(&full[b], (s / NS) & 1)) {
+                abort_flag = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;
+            const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
+#pragma unroll
+            for (int k = 0; k < KST / 16; ++k) {
+                const uint32_t off = k * 32;
+                const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
+                umma(tmem, sdesc(xa + off), sdesc(aa + off), idesc, first);   // hi . hi
+                umma(tmem, sdesc(xa + off), sdesc(ab + off), idesc, 1u);      // hi . lo
+                umma(tmem, sdesc(xb + off), sdesc(aa + off), idesc, 1u);      // lo . hi
+            }
+            umma_commit(&empty[b]);
+        }
+    }
+    __syncthreads();
+    if (!abort_flag && tk.nst > 0) {
+        const int last = tk.nst - 1;
+        if (!mbar_wait(&empty[last % NS], (last / NS) & 1)) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!abort_flag && tk.nst > 0) {
+        const int r = r0 + warp * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int j0 = 0; j0 < N; j0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(tl + (uint32_t)j0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (r < nrhs) {
+                float2 *o = out + (int64_t)r * ldo + tk.out_off;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int i = j0 / 2 + q;
+                    if (i < tk.m) {
+                        float2 val = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+                        if (beta_one) {
+                            const float2 p = o[i];
+                            val.x += p.x;
+                            val.y += p.y;
+                        }
+                        o[i] = val;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+size_t umma_ws_smem_bytes(int ns, int nmax) { return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 128) + 1024 + 128; }
+
 // Pack the real-expanded, bf16-split matrix images of every tile/stage.
 __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
                                  const int32_t *__restrict__ colmap, const float2 *__restrict__ mat,
@@ -376,6 +539,8 @@ static h2_status build_uphase(h2_handle *h, const Phase &ph, const std::vector<S
     }
     U.ntile = (int)tiles.size();
     U.image_bytes = img;
+    U.nmax = 16;
+    for (auto &u : tiles) U.nmax = std::max(U.nmax, u.n);
     if (U.ntile == 0) return H2_OK;
     UTask *d_tiles = nullptr;
     UPackInfo *d_info = nullptr;
@@ -407,6 +572,7 @@ static h2_status split_init(h2_handle *h)
 {
     if (h->split) return H2_OK;
     auto *S = new SplitState();
+    S->pipeline = h->tc_pipeline;
     // plane layouts: leaves of the tree order (near-field inputs) and cluster
     // coefficient blocks (coupling inputs), each padded to 4 complex entries
     std::vector<int32_t> leaf_pbase(h->nc, -1), coef_pbase(h->nc, -1);
@@ -476,6 +642,8 @@ static h2_status split_init(h2_handle *h)
     if ((st = build_uphase(h, h->couple, hsegs, cbase, S->couple)) != H2_OK) return st;
     UM_CUDA(cudaFuncSetAttribute(umma_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)umma_smem_bytes()));
+    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
     UM_CUDA(cudaMalloc(&S->d_err, sizeof(int)));
     UM_CUDA(cudaMemset(S->d_err, 0, sizeof(int)));
     return H2_OK;
@@ -513,6 +681,17 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_
 {
     if (U.ntile == 0) return cudaSuccess;
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
+    if (S->pipeline) {
+        const size_t limit = 232448;
+        if (umma_ws_smem_bytes(3, U.nmax) <= limit) {
+            umma_ws_kernel<3><<<grid, UT, umma_ws_smem_bytes(3, U.nmax), st>>>(
+                U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs, out, ldo, beta, U.nmax, S->d_err);
+        } else {
+            umma_ws_kernel<2><<<grid, UT, umma_ws_smem_bytes(2, U.nmax), st>>>(
+                U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs, out, ldo, beta, U.nmax, S->d_err);
+        }
+        return cudaGetLastError();
+    }
     umma_task_kernel<<<grid, UT, umma_smem_bytes(), st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs,
                                                           out, ldo, beta, S->d_err);
     return cudaGetLastError();
@@ -587,5 +766,13 @@ h2_status h2_split_error_flag(h2_handle *h, int *flag)
     *flag = 0;
     if (!h->split) return H2_OK;
     UM_CUDA(cudaMemcpy(flag, h->split->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return H2_OK;
+}
+
+h2_status h2_split_set_pipeline(h2_handle *h, int on)
+{
+    h2_status s = split_init(h);
+    if (s != H2_OK) return s;
+    h->split->pipeline = on != 0;
     return H2_OK;
 }

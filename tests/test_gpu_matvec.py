@@ -29,11 +29,11 @@ def loaded():
         m.close()
 
 
-def _mat(loaded, name, symmetric=False, dtype=np.complex128):
+def _mat(loaded, name, symmetric=False, dtype=np.complex128, tc_pipeline=True):
     from paper_1703_01175_gb300 import h2
-    key = (name, symmetric, dtype)
+    key = (name, symmetric, dtype, tc_pipeline)
     if key not in loaded:
-        loaded[key] = h2.H2Matrix(cases.get(name).arrays(dtype=dtype, symmetric=symmetric))
+        loaded[key] = h2.H2Matrix(cases.get(name).arrays(dtype=dtype, symmetric=symmetric), tc_pipeline=tc_pipeline)
     return loaded[key]
 
 
@@ -118,14 +118,16 @@ def test_multi_rhs_fp32_matches_oracle(loaded, name, R):
         assert np.linalg.norm(Y[:, j] - Y_or[:, j]) <= 1e-5 * np.linalg.norm(Y_or[:, j])
 
 
+@pytest.mark.parametrize("pipeline", [True, False])
 @pytest.mark.parametrize("name,R", [("cube12", 128), ("cube12", 5), ("ragged", 130), ("slab", 64),
                                     ("array", 17), ("tiny_leaves", 3)])
-def test_splitbf16_tensor_cores_match_oracle(loaded, name, R):
-    """Split-bf16 tcgen05 path: within eps = 1e-4 of the oracle's FP64 product
+def test_splitbf16_tensor_cores_match_oracle(loaded, name, R, pipeline):
+    """Split-bf16 tcgen05 path (warp-specialised multi-stage kernel and the
+    two-stage kernel): within eps = 1e-4 of the oracle's FP64 product
     (spec bound for the lower-precision form)."""
     from oracle import h2mv
     c = cases.get(name)
-    A = _mat(loaded, name)
+    A = _mat(loaded, name, tc_pipeline=pipeline)
     X = synth.random_complex(c.n, 12, cols=R)
     Y_or = h2mv.h2_dense(c.hZ) @ X
     for rep in range(2):

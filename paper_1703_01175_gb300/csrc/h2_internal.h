@@ -82,6 +82,7 @@ struct SplitState {
     int rcap = 0;
     int *d_err = nullptr;         // set when a bounded wait ran out
     bool pipeline = true;         // warp-specialised multi-stage kernel (else the two-stage one)
+    size_t dyn_smem_limit = 0;    // dynamic shared memory a block may use
 };
 
 void set_error(const std::string &msg);

@@ -642,8 +642,24 @@ static h2_status split_init(h2_handle *h)
     if ((st = build_uphase(h, h->couple, hsegs, cbase, S->couple)) != H2_OK) return st;
     UM_CUDA(cudaFuncSetAttribute(umma_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)umma_smem_bytes()));
-    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
-    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448));
+    {
+        // dynamic shared memory limit = opt-in per-block maximum minus the kernels' static shared memory
+        int optin = 0;
+        UM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
+        cudaFuncAttributes fa2{}, fa3{};
+        UM_CUDA(cudaFuncGetAttributes(&fa2, umma_ws_kernel<2>));
+        UM_CUDA(cudaFuncGetAttributes(&fa3, umma_ws_kernel<3>));
+        const size_t st = std::max(fa2.sharedSizeBytes, fa3.sharedSizeBytes);
+        S->dyn_smem_limit = optin > (int)st ? (size_t)optin - st : 0;
+        if (S->pipeline && umma_ws_smem_bytes(2, std::max(S->near.nmax, S->couple.nmax)) > S->dyn_smem_limit)
+            S->pipeline = false;  // tiles too wide for two stages: keep the two-stage kernel
+        if (S->pipeline) {
+            UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S->dyn_smem_limit));
+            UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S->dyn_smem_limit));
+        }
+    }
     UM_CUDA(cudaMalloc(&S->d_err, sizeof(int)));
     UM_CUDA(cudaMemset(S->d_err, 0, sizeof(int)));
     return H2_OK;
@@ -682,8 +698,7 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_
     if (U.ntile == 0) return cudaSuccess;
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
     if (S->pipeline) {
-        const size_t limit = 232448;
-        if (umma_ws_smem_bytes(3, U.nmax) <= limit) {
+        if (umma_ws_smem_bytes(3, U.nmax) <= S->dyn_smem_limit) {
             umma_ws_kernel<3><<<grid, UT, umma_ws_smem_bytes(3, U.nmax), st>>>(
                 U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs, out, ldo, beta, U.nmax, S->d_err);
         } else {

@@ -94,6 +94,12 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def construct_cached(w):
+    from paper_1703_01175_gb300 import construct
+    v = w.voxels
+    return construct.build_vie_h2_cached(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
+
+
 def build_workload(name: str):
     """H^2 arrays of the workload from the host constructor (setup, cached on
     disk between runs). Returns (workload, arrays, tree permutation, seconds)."""
@@ -324,6 +330,43 @@ def run_ours(args, rank, world, local_rank):
                              "products": "split-bf16 tensor cores, FP64 CGS2, FP64-accumulated restart residuals"}
         gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
 
+    # learned preconditioner (shipped weights, trained by train_precond on the 16^3 cube): flexible
+    # GMRES(50) with M(v) = v + N(v) against plain GMRES(50), on the bench cube and on the training cube
+    wpath = os.path.join(ROOT, "paper_1703_01175_gb300", "weights", "vie_u26.npz")
+    if args.learned and os.path.exists(wpath):
+        from paper_1703_01175_gb300 import precond as P
+        z = np.load(wpath)
+        layers = [tuple(int(v) for v in x) for x in z["layers"]]
+        Wl = [z[f"W{i}"] for i in range(len(layers))]
+        Bl = [z[f"b{i}"] for i in range(len(layers))]
+        learned = {"weights": os.path.relpath(wpath, ROOT), "n_params": int(sum(x.size for x in Wl) + sum(x.size for x in Bl))}
+        for wname in ("cube16r", WORKLOAD):
+            if wname == WORKLOAD:
+                Aw, pw, ww = A, perm, w
+            else:
+                ww = synth.workload(wname)
+                aw, pw = construct_cached(ww)
+                Aw = h2py.H2Matrix(aw, device=local_rank)
+            gmw = P.GridMap(ww.voxels.shape, pw, ww.voxels.eps_r)
+            P.load_into(Aw, layers, Wl, Bl, gmw)
+            bw = torch.from_numpy(synth.default_rhs(ww)[(3 * pw[:, None] + np.arange(3)[None, :]).reshape(-1)]).to(dev)
+            row = {}
+            for label, pc in (("plain", 0), ("fgmres_learned", 1)):
+                torch.cuda.synchronize(dev)
+                g0 = torch.cuda.Event(enable_timing=True)
+                g1 = torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                xs, info = Aw.gmres(bw, tol=ww.tol, restart=50, maxit=2000, refine=True, precond=pc)
+                g1.record(stream)
+                torch.cuda.synchronize(dev)
+                row[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
+                              "rel_res": info[0]["rel_res"], "status": info[0]["status"],
+                              "precond_cycles": info[0]["precond_cycles"]}
+            learned[wname] = row
+            if Aw is not A:
+                Aw.close()
+        gm["learned"] = learned
+
     # end to end through the host-pointer entry point
     for _ in range(2):
         A.matvec_host(x_np)
@@ -387,7 +430,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--gmres-batch", type=int, default=16, help="right-hand sides of the batched solve (0: skip)")
+    ap.add_argument("--no-learned", dest="learned", action="store_false",
+                    help="skip the learned-preconditioner leg")
+    ap.add_argument("--gmres-batch", type=int, default=32, help="right-hand sides of the batched solve (0: skip)")
     ap.add_argument("--gmres-restart", type=int, default=400, help="restart of the batched / plain comparison")
     ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")

@@ -184,9 +184,25 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w, arrs, perm, t_build = build_workload(args.workload)
     A = h2py.H2Matrix(arrs, device=local_rank)
+    n = arrs.n
+    if args.only_mrhs:
+        # profiling mode: the split-bf16 multi-RHS product alone (no autotuner
+        # trial launches, no single-RHS product before it)
+        R = max(1, args.mrhs)
+        Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
+        Xm = Xm.to(dev).t().contiguous().t()
+        Ym = torch.empty_like(Xm)
+        for _ in range(args.warmup + args.steps):
+            A.matvec(Xm, Ym, prec="splitbf16")
+        torch.cuda.synchronize(dev)
+        status = A.device_status()
+        A.close()
+        if rank == 0:
+            print(json.dumps({"only_mrhs": True, "nrhs": R, "workload": args.workload, "status": status}), flush=True)
+        return
+
     tuning = A.autotune()
     st = A.stats()
-    n = arrs.n
     x_np = synth.random_complex(n, 1).astype(np.complex64)
     x = torch.from_numpy(x_np).to(dev)
     y = torch.empty_like(x)
@@ -216,20 +232,6 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-
-    if args.only_mrhs:
-        R = max(1, args.mrhs)
-        Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
-        Xm = Xm.to(dev).t().contiguous().t()
-        Ym = torch.empty_like(Xm)
-        for _ in range(args.warmup + args.steps):
-            A.matvec(Xm, Ym, prec="splitbf16")
-        torch.cuda.synchronize(dev)
-        status = A.device_status()
-        A.close()
-        if rank == 0:
-            print(json.dumps({"only_mrhs": True, "nrhs": R, "workload": args.workload, "status": status}), flush=True)
-        return
 
     if args.only_matvec:
         A.close()

@@ -230,13 +230,15 @@ typedef struct {
     double rel_res;     /* final true relative residual ||b - A x|| / ||b|| */
     int32_t status;     /* H2_OK, H2_ERR_NOT_CONVERGED or H2_ERR_BREAKDOWN */
     int32_t precond_cycles; /* cycles run with the preconditioner (flexible GMRES) */
+    int32_t reorth_steps;   /* Arnoldi steps that needed the second Gram-Schmidt projection */
 } h2_solve_info;
 
 /*
  * Solve A x = b by restarted GMRES(m) (Saad & Schultz) around the H^2
- * product: Arnoldi with classical Gram-Schmidt applied twice in FP64 on c128
- * vectors, Givens rotations and the Hessenberg least-squares solve on the
- * device, FP32 H^2 products inside the cycles. Each restart recomputes the
+ * product: FP64 Arnoldi on c128 vectors (classical Gram-Schmidt with selective
+ * reorthogonalisation: a second projection when the first one cancels more
+ * than half of |w|^2), Givens rotations and the Hessenberg least-squares solve
+ * on the device, FP32 H^2 products inside the cycles. Each restart recomputes the
  * true residual (FP64-accumulated product when opts->refine). The paper's own
  * solver is BiCGStab (Sec. V); this is the Krylov method around the same
  * product (Sec. IV.B).
@@ -255,8 +257,8 @@ h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t l
  * each with its own Krylov basis, Hessenberg matrix and Givens rotations, so
  * every Arnoldi step runs ONE multi-RHS product (prec = H2_PREC_FP32: CUDA-core
  * complex GEMMs; H2_PREC_SPLITBF16: tensor cores) and the FP64 Gram-Schmidt
- * (CGS2), rotation and back-substitution kernels are batched over the
- * right-hand sides. A right-hand side whose residual estimate drops below
+ * (selective reorthogonalisation, as in h2_gmres), rotation and
+ * back-substitution kernels are batched over the right-hand sides. A right-hand side whose residual estimate drops below
  * tol / 2 stops contributing at the end of the cycle. Restart residuals:
  * FP64-accumulated products when opts->refine (one per right-hand side),
  * else one batched product with `prec`. opts->precond must be 0.

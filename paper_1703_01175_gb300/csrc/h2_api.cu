@@ -240,6 +240,7 @@ void h2_free(h2_handle *h)
     cudaFree(h->d_tasks);
     cudaFree(h->d_coef);
     cudaFree(h->d_coefm);
+    cudaFree(h->d_colidx);
     cudaFree(h->d_xbuf);
     cudaFree(h->d_ybuf);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);

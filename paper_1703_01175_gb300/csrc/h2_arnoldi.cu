@@ -1,0 +1,585 @@
+// FP64 Arnoldi process of restarted GMRES for R right-hand sides at once
+// (R = 1 for the single-RHS solver). Each right-hand side owns its Krylov
+// basis, Hessenberg matrix and Givens rotations; every kernel is batched over
+// the right-hand sides with blockIdx.y = right-hand side.
+//
+// Orthogonalisation is classical Gram-Schmidt with selective
+// reorthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): after one
+// projection w' = w - V (V^H w), a second projection runs only when
+// |w'| < |w| / sqrt(2), i.e. when cancellation may have cost orthogonality.
+// With no reorthogonalisation the step reads the basis twice (one dot pass,
+// one update pass) instead of the four reads of CGS applied twice.
+//
+// Dot pass V^H w: one block per (basis column, row segment), so each block
+// streams a long contiguous run of one column and reduces inside the block;
+// only (columns x segments) partial sums remain, and the segment count shrinks
+// as the basis grows (one segment per column once the grid is full). Update
+// pass w - V h: blocks over rows, each thread sweeps the basis for its rows.
+// Cross-block sums are combined in a fixed order by the last block to finish
+// (a ticket counter), so results are bitwise reproducible.
+//
+// The small dense part of GMRES (Hessenberg column, Givens rotations,
+// residual estimate, back-substitution) runs in FP64 on the host: each step
+// already synchronises to test convergence, the coefficients of a step are a
+// few kilobytes, and a sequential rotation sweep on one GPU thread would sit
+// on GB300's narrow FP64 pipe.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <string>
+
+#include "h2_internal.h"
+
+namespace h2 {
+namespace {
+
+constexpr int AT = 256;       // threads per block
+constexpr int NW = AT / 32;
+constexpr int TARGET = 4 * 152;  // blocks that fill the GPU
+constexpr double REORTH2 = 0.5;  // reorthogonalise when |w'|^2 < REORTH2 |w|^2
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 wsum(double2 v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
+
+// block-wide sum (all threads get the result)
+__device__ double2 block_sum(double2 v)
+{
+    __shared__ double2 red[NW];
+    __shared__ double2 tot;
+    v = wsum(v);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 s = red[0];
+        for (int q = 1; q < NW; ++q) s = zadd(s, red[q]);
+        tot = s;
+    }
+    __syncthreads();
+    return tot;
+}
+
+// true in the last block of right-hand side r to pass (resets the counter)
+__device__ bool last_of_rhs(unsigned *ticket)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(ticket, 1u) == (unsigned)gridDim.x - 1;
+        if (last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+__device__ __forceinline__ double2 vload(const volatile double2 *p)
+{
+    return make_double2(p->x, p->y);
+}
+
+// out[c] = sum_{s < S} part[c * S + s] for c < ncols (fixed order)
+__device__ void reduce_columns(const double2 *part, int ncols, int S, double2 *out)
+{
+    const volatile double2 *p = part;
+    if (S >= 8) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int c = warp; c < ncols; c += NW) {
+            double2 a = make_double2(0, 0);
+            for (int s = lane; s < S; s += 32) a = zadd(a, vload(p + (size_t)c * S + s));
+            a = wsum(a);
+            if (lane == 0) out[c] = a;
+        }
+    } else {
+        for (int c = threadIdx.x; c < ncols; c += AT) {
+            double2 a = make_double2(0, 0);
+            for (int s = 0; s < S; ++s) a = zadd(a, vload(p + (size_t)c * S + s));
+            out[c] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// conj(v) * w accumulated with four FMAs
+__device__ __forceinline__ void cmac_conj(double2 &acc, double2 v, double2 w)
+{
+    acc.x = fma(v.x, w.x, acc.x);
+    acc.x = fma(v.y, w.y, acc.x);
+    acc.y = fma(v.x, w.y, acc.y);
+    acc.y = fma(-v.y, w.x, acc.y);
+}
+
+// acc -= v * h with four FMAs
+__device__ __forceinline__ void cmsub(double2 &acc, double2 v, double2 h)
+{
+    acc.x = fma(-v.x, h.x, acc.x);
+    acc.x = fma(v.y, h.y, acc.x);
+    acc.y = fma(-v.x, h.y, acc.y);
+    acc.y = fma(-v.y, h.x, acc.y);
+}
+
+// w = c128(y32) (the product of the step, widened once)
+__global__ void arn_widen(ArnDev K, const float2 *__restrict__ y32)
+{
+    const int r = blockIdx.y;
+    const float2 *y = y32 + (size_t)r * K.n;
+    double2 *w = K.w + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x)
+        w[i] = make_double2(y[i].x, y[i].y);
+}
+
+// Dot pass: coefficients V^H w for columns 0..j. FIRST also forms |w|^2
+// (pseudo-column j+1) into h1[j+1]; SECOND runs only for right-hand sides
+// flagged for reorthogonalisation and writes h2.
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_dot(ArnDev K, int j, int S, int seg)
+{
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const int l = blockIdx.x / S, s = blockIdx.x - l * S;
+    const int i0 = s * seg, i1 = min(K.n, i0 + seg);
+    const double2 *w = K.w + (size_t)r * K.n;
+    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+    if (l <= j) {
+        const double2 *Vl = K.V + ((size_t)l * K.R + r) * K.n;
+        int i = i0 + threadIdx.x;
+        for (; i + AT < i1; i += 2 * AT) {
+            cmac_conj(acc0, ld_stream(Vl + i), w[i]);
+            cmac_conj(acc1, ld_stream(Vl + i + AT), w[i + AT]);
+        }
+        if (i < i1) cmac_conj(acc0, ld_stream(Vl + i), w[i]);
+    } else {  // FIRST only: |w|^2 over the segment
+        for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+            const double2 v = w[i];
+            acc0.x = fma(v.x, v.x, acc0.x);
+            acc0.x = fma(v.y, v.y, acc0.x);
+        }
+    }
+    const double2 tot = block_sum(zadd(acc0, acc1));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 2 : 0))) return;
+    const int ncols = SECOND ? j + 1 : j + 2;
+    reduce_columns(part, ncols, S, (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2));
+}
+
+// Update pass w -= V h (h = h1, or h2 in the second pass). The last block
+// forms |w|^2; the first pass decides whether the right-hand side needs the
+// second projection (flag scal[3]); the pass that ends the step stores
+// beta = |w| in scal[0]. Dynamic shared memory: m + 2 complex entries.
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_update(ArnDev K, int j, int rows)
+{
+    extern __shared__ double2 hs[];
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const double2 *h = (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2);
+    for (int l = threadIdx.x; l <= j; l += AT) hs[l] = h[l];
+    __syncthreads();
+    const int i0 = blockIdx.x * rows, i1 = min(K.n, i0 + rows);
+    double2 *w = K.w + (size_t)r * K.n;
+    const double2 *V = K.V + (size_t)r * K.n;
+    const size_t ldv = (size_t)K.R * K.n;
+    double nrm = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+        double2 acc = w[i];
+        int l = 0;
+        for (; l + 1 <= j; l += 2) {
+            const double2 a = ld_stream(V + (size_t)l * ldv + i), b = ld_stream(V + (size_t)(l + 1) * ldv + i);
+            cmsub(acc, a, hs[l]);
+            cmsub(acc, b, hs[l + 1]);
+        }
+        if (l <= j) cmsub(acc, ld_stream(V + (size_t)l * ldv + i), hs[l]);
+        w[i] = acc;
+        nrm = fma(acc.x, acc.x, nrm);
+        nrm = fma(acc.y, acc.y, nrm);
+    }
+    const double2 tot = block_sum(make_double2(nrm, 0.0));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 3 : 1))) return;
+    double s = 0.0;
+    const volatile double2 *p = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += AT) s += p[b].x;
+    const double nw2 = block_sum(make_double2(s, 0.0)).x;
+    if (threadIdx.x != 0) return;
+    if (!SECOND) {
+        const double rho = K.h1[(size_t)r * (K.m + 2) + j + 1].x;  // |w|^2 before the projection
+        const bool again = !(nw2 >= REORTH2 * rho);
+        K.scal[8 * r + 3] = again ? 1.0 : 0.0;
+        if (again) return;
+    }
+    K.scal[8 * r] = sqrt(nw2);
+}
+
+// v_{jn} = w / beta (c128 into the basis, c64 into x32 for the next product)
+__global__ void arn_normalize(ArnDev K, int jn, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    double2 *Vn = K.V + ((size_t)jn * K.R + r) * K.n;
+    const double2 *w = K.w + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const double2 v = w[i];
+        const double2 q = make_double2(v.x * inv, v.y * inv);
+        Vn[i] = q;
+        x[i] = make_float2((float)q.x, (float)q.y);
+    }
+}
+
+// rr = b - y (y may be NULL); |rr| -> scal[8 r]
+__global__ void __launch_bounds__(AT) arn_residual(ArnDev K, const double2 *__restrict__ b, int64_t ldb,
+                                                   const double2 *__restrict__ y, double2 *__restrict__ rr, int rows)
+{
+    const int r = blockIdx.y;
+    const int i0 = blockIdx.x * rows, i1 = min(K.n, i0 + rows);
+    double nrm = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+        double2 v = b[(size_t)r * ldb + i];
+        if (y) v = zsub(v, y[(size_t)r * K.n + i]);
+        rr[(size_t)r * K.n + i] = v;
+        nrm += v.x * v.x + v.y * v.y;
+    }
+    const double2 tot = block_sum(make_double2(nrm, 0.0));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + 4)) return;
+    double s = 0.0;
+    const volatile double2 *p = part;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += AT) s += p[q].x;
+    const double t = block_sum(make_double2(s, 0.0)).x;
+    if (threadIdx.x == 0) K.scal[8 * r] = sqrt(t);
+}
+
+// start a cycle: v_0 = rr / beta, x32 = c64(v_0)
+__global__ void arn_start(ArnDev K, const double2 *__restrict__ rr, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    double2 *V0 = K.V + (size_t)r * K.n;
+    const double2 *v = rr + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const double2 q = make_double2(v[i].x * inv, v[i].y * inv);
+        V0[i] = q;
+        x[i] = make_float2((float)q.x, (float)q.y);
+    }
+}
+
+// x += B y with B = V (GMRES) or Z (flexible GMRES), B laid out like V; y in h1
+__global__ void arn_xupdate(ArnDev K, const double2 *__restrict__ basis, double2 *__restrict__ x, int64_t ldx)
+{
+    extern __shared__ double2 ys[];
+    const int r = blockIdx.y;
+    const int k = K.kact[r];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = K.h1[(size_t)r * (K.m + 2) + l];
+    __syncthreads();
+    if (k == 0) return;
+    const size_t ldb = (size_t)K.R * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        double2 acc = x[(size_t)r * ldx + i];
+        for (int l = 0; l < k; ++l) acc = zadd(acc, zmul(basis[(size_t)l * ldb + (size_t)r * K.n + i], ys[l]));
+        x[(size_t)r * ldx + i] = acc;
+    }
+}
+
+__global__ void arn_to_c64(const double2 *__restrict__ a, int64_t lda, float2 *__restrict__ b, int n)
+{
+    const int r = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 v = a[(size_t)r * lda + i];
+        b[(size_t)r * n + i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+__global__ void arn_to_c128(const float2 *__restrict__ a, double2 *__restrict__ b, int n)
+{
+    const int r = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 v = a[(size_t)r * n + i];
+        b[(size_t)r * n + i] = make_double2(v.x, v.y);
+    }
+}
+
+// segments of the dot pass at step j: enough blocks to fill the GPU
+void dot_split(int n, int R, int j, int *S, int *seg)
+{
+    const int cols = j + 2;
+    int s = (TARGET + cols * R - 1) / (cols * R);
+    s = std::max(1, std::min(s, std::max(1, n / 1024)));
+    int sg = (n + s - 1) / s;
+    sg = (sg + 31) / 32 * 32;
+    *seg = std::max(32, sg);
+    *S = (n + *seg - 1) / *seg;
+}
+
+}  // namespace
+
+#define ARNC(call)                                                                    \
+    do {                                                                              \
+        cudaError_t e__ = (call);                                                     \
+        if (e__ != cudaSuccess) {                                                     \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));           \
+            return H2_ERR_CUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+void arn_free(ArnWork *w)
+{
+    if (!w) return;
+    cudaFree(w->block);
+    cudaFreeHost(w->h_scal);
+    cudaFreeHost(w->h_kact);
+    cudaFreeHost(w->h_hh);
+    delete w;
+}
+
+h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols)
+{
+    ArnWork *w = *slot;
+    if (w && w->n == n && w->m == m && w->R == R && w->extra_cols == extra_cols) return H2_OK;
+    arn_free(w);
+    *slot = nullptr;
+    w = new ArnWork();
+    w->n = n;
+    w->m = m;
+    w->R = R;
+    w->extra_cols = extra_cols;
+    // update / residual grid: rows per block, multiple of 32
+    int nb = std::max(1, std::min((n + AT - 1) / AT, (TARGET + R - 1) / R));
+    int rows = (n + nb - 1) / nb;
+    rows = (rows + 31) / 32 * 32;
+    w->rows = rows;
+    w->nbu = (n + rows - 1) / rows;
+    int np = w->nbu;
+    for (int j = 0; j < m; ++j) {
+        int S, seg;
+        dot_split(n, R, j, &S, &seg);
+        np = std::max(np, (j + 2) * S);
+    }
+    ArnDev &K = w->K;
+    K.n = n;
+    K.m = m;
+    K.R = R;
+    K.np = np;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t hh = (size_t)2 * R * (m + 2);  // h1 rows, then h2 rows
+    const size_t oV = take(sizeof(double2) * (size_t)n * (m + 1) * R);
+    const size_t oZ = extra_cols ? take(sizeof(double2) * (size_t)n * extra_cols * R) : 0;
+    const size_t ow = take(sizeof(double2) * (size_t)n * R);
+    const size_t op = take(sizeof(double2) * (size_t)np * R);
+    const size_t ot = take(sizeof(unsigned) * 8 * R);
+    const size_t oh = take(sizeof(double2) * hh);
+    const size_t osc = take(sizeof(double) * 8 * R);
+    const size_t ok = take(sizeof(int) * R);
+    const size_t orr = take(sizeof(double2) * (size_t)n * R);
+    const size_t otm = take(sizeof(double2) * (size_t)n * R);
+    const size_t ox = take(sizeof(float2) * (size_t)n * R);
+    const size_t oy = take(sizeof(float2) * (size_t)n * R);
+    if (cudaMalloc(&w->block, off) != cudaSuccess || cudaMallocHost(&w->h_scal, 8 * sizeof(double) * R) != cudaSuccess ||
+        cudaMallocHost(&w->h_kact, sizeof(int) * R) != cudaSuccess ||
+        cudaMallocHost(&w->h_hh, sizeof(double2) * hh) != cudaSuccess) {
+        arn_free(w);
+        set_error("GMRES workspace allocation failed (" + std::to_string(off >> 20) + " MiB)");
+        return H2_ERR_ALLOC;
+    }
+    char *base = reinterpret_cast<char *>(w->block);
+    K.V = reinterpret_cast<double2 *>(base + oV);
+    w->Z = extra_cols ? reinterpret_cast<double2 *>(base + oZ) : nullptr;
+    K.w = reinterpret_cast<double2 *>(base + ow);
+    K.part = reinterpret_cast<double2 *>(base + op);
+    K.ticket = reinterpret_cast<unsigned *>(base + ot);
+    K.h1 = reinterpret_cast<double2 *>(base + oh);
+    K.h2 = K.h1 + (size_t)R * (m + 2);
+    K.scal = reinterpret_cast<double *>(base + osc);
+    K.kact = reinterpret_cast<int *>(base + ok);
+    w->rr = reinterpret_cast<double2 *>(base + orr);
+    w->tmp = reinterpret_cast<double2 *>(base + otm);
+    w->x32 = reinterpret_cast<float2 *>(base + ox);
+    w->y32 = reinterpret_cast<float2 *>(base + oy);
+    if (cudaMemset(K.ticket, 0, sizeof(unsigned) * 8 * R) != cudaSuccess ||
+        cudaMemset(K.scal, 0, sizeof(double) * 8 * R) != cudaSuccess) {
+        arn_free(w);
+        return H2_ERR_CUDA;
+    }
+    const int smem = (int)(sizeof(double2) * (m + 2));
+    if (cudaFuncSetAttribute(arn_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(arn_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaFuncSetAttribute(arn_xupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        arn_free(w);
+        set_error("GMRES: shared-memory attribute rejected");
+        return H2_ERR_CUDA;
+    }
+    w->H.assign((size_t)R * m * (m + 1), 0.0);
+    w->g.assign((size_t)R * (m + 1), 0.0);
+    w->sn.assign((size_t)R * m, 0.0);
+    w->cs.assign((size_t)R * m, 0.0);
+    w->est.assign(R, 0.0);
+    w->beta.assign(R, 0.0);
+    w->bad.assign(R, 0);
+    w->reorth.assign(R, 0);
+    *slot = w;
+    return H2_OK;
+}
+
+static dim3 vec_grid(const ArnWork *w) { return dim3(std::min(1024, (w->n + 255) / 256), w->R); }
+
+h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st)
+{
+    arn_residual<<<dim3(w->nbu, w->R), AT, 0, st>>>(w->K, b, ldb, y, w->rr, w->rows);
+    ARNC(cudaGetLastError());
+    return H2_OK;
+}
+
+h2_status arn_start(ArnWork *w, cudaStream_t st)
+{
+    arn_start<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
+    ARNC(cudaGetLastError());
+    const int m = w->m;
+    for (int r = 0; r < w->R; ++r) {
+        std::complex<double> *g = w->g.data() + (size_t)r * (m + 1);
+        std::fill(g, g + m + 1, 0.0);
+        g[0] = w->h_scal[8 * r];
+    }
+    return H2_OK;
+}
+
+// Hessenberg column j of right-hand side r on the host: coefficients of the
+// projection(s), subdiagonal beta, previous rotations, new rotation, rotated
+// right-hand side and residual estimate |g_{j+1}|.
+static void host_column(ArnWork *w, int r, int j)
+{
+    using C = std::complex<double>;
+    const int m = w->m, R = w->R;
+    const double2 *h1 = w->h_hh + (size_t)r * (m + 2);
+    const double2 *h2 = w->h_hh + (size_t)(R + r) * (m + 2);
+    const double *sc = w->h_scal + 8 * r;
+    const bool again = sc[3] != 0.0;
+    const double beta = sc[0];
+    C *Hj = w->H.data() + ((size_t)r * m + j) * (m + 1);
+    double *cs = w->cs.data() + (size_t)r * m;
+    C *sn = w->sn.data() + (size_t)r * m;
+    C *g = w->g.data() + (size_t)r * (m + 1);
+    for (int l = 0; l <= j; ++l) {
+        Hj[l] = C(h1[l].x, h1[l].y);
+        if (again) Hj[l] += C(h2[l].x, h2[l].y);
+    }
+    for (int l = 0; l < j; ++l) {  // rotation l: [c s; -conj(s) c]
+        const C a = Hj[l], b = Hj[l + 1];
+        Hj[l] = cs[l] * a + sn[l] * b;
+        Hj[l + 1] = cs[l] * b - std::conj(sn[l]) * a;
+    }
+    const C a = Hj[j];
+    const double na = std::abs(a);
+    double c;
+    C s;
+    if (beta == 0.0) {
+        c = 1.0;
+        s = 0.0;
+    } else if (na == 0.0) {
+        c = 0.0;
+        s = 1.0;
+    } else {
+        const double nr = std::hypot(na, beta);
+        c = na / nr;
+        s = a / na * (beta / nr);
+    }
+    cs[j] = c;
+    sn[j] = s;
+    Hj[j] = c * a + s * beta;
+    Hj[j + 1] = 0.0;
+    g[j + 1] = -std::conj(s) * g[j];
+    g[j] = c * g[j];
+    w->beta[r] = beta;
+    w->est[r] = std::abs(g[j + 1]);
+    w->reorth[r] = again;
+    w->bad[r] = !std::isfinite(beta) || !std::isfinite(w->est[r]);
+}
+
+h2_status arn_step(ArnWork *w, int j, cudaStream_t st)
+{
+    const ArnDev &K = w->K;
+    int S, seg;
+    dot_split(w->n, w->R, j, &S, &seg);
+    const size_t smem = sizeof(double2) * (w->m + 2);
+    arn_widen<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
+    arn_dot<false><<<dim3((j + 2) * S, w->R), AT, 0, st>>>(K, j, S, seg);
+    arn_update<false><<<dim3(w->nbu, w->R), AT, smem, st>>>(K, j, w->rows);
+    arn_dot<true><<<dim3((j + 1) * S, w->R), AT, 0, st>>>(K, j, S, seg);
+    arn_update<true><<<dim3(w->nbu, w->R), AT, smem, st>>>(K, j, w->rows);
+    arn_normalize<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+    ARNC(cudaGetLastError());
+    ARNC(cudaMemcpyAsync(w->h_hh, K.h1, sizeof(double2) * 2 * w->R * (w->m + 2), cudaMemcpyDeviceToHost, st));
+    ARNC(cudaMemcpyAsync(w->h_scal, K.scal, 8 * sizeof(double) * w->R, cudaMemcpyDeviceToHost, st));
+    ARNC(cudaStreamSynchronize(st));
+    for (int r = 0; r < w->R; ++r) host_column(w, r, j);
+    return H2_OK;
+}
+
+h2_status arn_read(ArnWork *w, cudaStream_t st)
+{
+    ARNC(cudaMemcpyAsync(w->h_scal, w->K.scal, 8 * sizeof(double) * w->R, cudaMemcpyDeviceToHost, st));
+    ARNC(cudaStreamSynchronize(st));
+    return H2_OK;
+}
+
+h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, cudaStream_t st)
+{
+    using C = std::complex<double>;
+    const int m = w->m;
+    for (int r = 0; r < w->R; ++r) {  // y = H(1:k,1:k)^{-1} g(1:k) by back substitution
+        const int k = w->h_kact[r];
+        const C *H = w->H.data() + (size_t)r * m * (m + 1), *g = w->g.data() + (size_t)r * (m + 1);
+        double2 *y = w->h_hh + (size_t)r * (m + 2);
+        std::vector<C> yc(std::max(k, 1));
+        for (int i = k - 1; i >= 0; --i) {
+            C s = g[i];
+            for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * yc[l];
+            const C d = H[(size_t)i * (m + 1) + i];
+            yc[i] = std::norm(d) > 0.0 ? s / d : C(0.0);
+            y[i] = make_double2(yc[i].real(), yc[i].imag());
+        }
+    }
+    ARNC(cudaMemcpyAsync(w->K.h1, w->h_hh, sizeof(double2) * w->R * (m + 2), cudaMemcpyHostToDevice, st));
+    ARNC(cudaMemcpyAsync(w->K.kact, w->h_kact, sizeof(int) * w->R, cudaMemcpyHostToDevice, st));
+    arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
+    ARNC(cudaGetLastError());
+    return H2_OK;
+}
+
+h2_status arn_c128_to_c64(ArnWork *w, const double2 *a, int64_t lda, float2 *b, cudaStream_t st)
+{
+    arn_to_c64<<<vec_grid(w), 256, 0, st>>>(a, lda, b, w->n);
+    ARNC(cudaGetLastError());
+    return H2_OK;
+}
+
+h2_status arn_c64_to_c128(ArnWork *w, const float2 *a, double2 *b, cudaStream_t st)
+{
+    arn_to_c128<<<vec_grid(w), 256, 0, st>>>(a, b, w->n);
+    ARNC(cudaGetLastError());
+    return H2_OK;
+}
+
+}  // namespace h2

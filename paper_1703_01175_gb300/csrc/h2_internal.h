@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -42,6 +43,8 @@ struct Phase {
     int32_t max_ncol = 0;
     int64_t elems = 0;             // matrix entries streamed (sum of m * ncol)
     int threads = 256;
+    int32_t *d_coloff = nullptr;   // multi-RHS path: first entry of each task in d_colidx
+    const int32_t *d_colidx = nullptr;  // multi-RHS path: input index of every task column (handle's table)
     int ntask() const { return (int)tasks.size(); }
 };
 
@@ -87,6 +90,52 @@ struct SplitState {
 
 void set_error(const std::string &msg);
 
+// FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
+struct ArnDev {
+    double2 *V;        // basis [(m+1)][R][n]
+    double2 *w;        // [R][n] vector being orthogonalised
+    double2 *part;     // [R][np] partial sums of the reductions
+    unsigned *ticket;  // [R][8] last-block counters
+    double2 *h1, *h2;  // [R][m+2] projection coefficients (h1[j+1] = |w|^2); h2 follows h1
+    double *scal;      // [R][8]: beta, -, -, reorthogonalised flag
+    int *kact;         // [R] basis columns used by the update of x
+    int n, m, R, np;
+};
+
+struct ArnWork {
+    ArnDev K{};
+    int n = 0, m = 0, R = 0, extra_cols = 0;
+    int rows = 0, nbu = 0;          // row blocks of the update and residual passes
+    double2 *Z = nullptr;           // [extra_cols][R][n] preconditioned directions (flexible GMRES)
+    double2 *rr = nullptr, *tmp = nullptr;  // [R][n]
+    float2 *x32 = nullptr, *y32 = nullptr;  // [R][n] product input / output
+    double *h_scal = nullptr;       // pinned copy of scal
+    int *h_kact = nullptr;          // pinned kact
+    double2 *h_hh = nullptr;        // pinned copy of h1, h2 (and the least-squares solution)
+    void *block = nullptr;
+    // host FP64 least-squares state per right-hand side
+    std::vector<std::complex<double>> H, g, sn;  // [R][m][m+1] rotated Hessenberg, [R][m+1], [R][m]
+    std::vector<double> cs;                      // [R][m]
+    std::vector<double> est, beta;               // after a step: |g_{j+1}|, |w|
+    std::vector<char> bad, reorth;               // after a step: non-finite, second projection taken
+};
+
+h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols);
+void arn_free(ArnWork *w);
+// rr = b - y (y NULL: rr = b); scal[8 r] = |rr_r|
+h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st);
+// v_0 = rr / |rr|, x32 = c64(v_0), g = |rr| e_1 (|rr| from h_scal: call arn_read first)
+h2_status arn_start(ArnWork *w, cudaStream_t st);
+// with y32 = A x32: orthogonalise, v_{j+1} and x32 = c64(v_{j+1}); then (host)
+// Hessenberg column j, rotations, est / beta / bad / reorth per right-hand side
+h2_status arn_step(ArnWork *w, int j, cudaStream_t st);
+// copy scal to h_scal and synchronise
+h2_status arn_read(ArnWork *w, cudaStream_t st);
+// least-squares solve (host) with h_kact columns, x_r += basis_r y_r
+h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, cudaStream_t st);
+h2_status arn_c128_to_c64(ArnWork *w, const double2 *a, int64_t lda, float2 *b, cudaStream_t st);
+h2_status arn_c64_to_c128(ArnWork *w, const float2 *a, double2 *b, cudaStream_t st);
+
 }  // namespace h2
 
 struct h2_handle {
@@ -117,6 +166,7 @@ struct h2_handle {
 
     void *krylov = nullptr;       // GMRES workspace (h2_krylov.cu)
     void *d_coefm = nullptr;      // multi-RHS coefficients (2 ktot x R, h2_mrhs.cu)
+    int32_t *d_colidx = nullptr;  // multi-RHS path: input index of every task column, all phases (h2_mrhs.cu)
     int64_t coefm_bytes = 0;
     std::vector<h2::Seg> segs_host;   // host copy of the input segments (split-bf16 packing)
     void *precond = nullptr;          // learned preconditioner (h2_precond.cu)
@@ -138,6 +188,8 @@ struct h2_handle {
 
 void h2_free_krylov(h2_handle *h);
 h2_status h2_ensure_coefm(h2_handle *h, int nrhs);
+// column index tables of every phase for the multi-RHS kernels (built once)
+h2_status h2_ensure_colidx(h2_handle *h);
 void h2_free_split(h2_handle *h);
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st);
@@ -155,9 +207,9 @@ namespace h2 {
 cudaError_t launch_phase_f32(const Phase &ph, const float2 *mat, const Seg *segs,
                              const float2 *in0, const float2 *in1, float2 *out,
                              int beta_one, cudaStream_t st);
-cudaError_t launch_phase_mrhs_f32(const Phase &ph, const float2 *mat, const Seg *segs, const float2 *in0,
-                                  int64_t ld0, const float2 *in1, int64_t ld1, float2 *out, int64_t ldo, int nrhs,
-                                  int beta_one, cudaStream_t st);
+cudaError_t launch_phase_mrhs_f32(const Phase &ph, const float2 *mat, const float2 *in0, int64_t ld0,
+                                  const float2 *in1, int64_t ld1, float2 *out, int64_t ldo, int nrhs, int beta_one,
+                                  cudaStream_t st);
 cudaError_t launch_phase_f64(const Phase &ph, const float2 *mat, const Seg *segs,
                              const double2 *in0, const double2 *in1, double2 *out,
                              int beta_one, cudaStream_t st);

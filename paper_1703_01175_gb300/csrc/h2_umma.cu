@@ -745,10 +745,10 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     const int rpad = (nrhs + MT - 1) / MT * MT;
     if ((s = ensure_planes(h, rpad)) != H2_OK) return s;
     if ((s = h2_ensure_coefm(h, nrhs)) != H2_OK) return s;
+    if ((s = h2_ensure_colidx(h)) != H2_OK) return s;
     const int64_t ldc = std::max<int64_t>(2, 2 * h->ktot);
     float2 *coef = reinterpret_cast<float2 *>(h->d_coefm);
     const float2 *mat = h->d_mat;
-    const Seg *segs = h->d_segs;
     const int64_t ldpx = 2 * S->np_x, ldpc = 2 * S->np_c;
     UM_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * ldc * nrhs, st));
     {
@@ -760,9 +760,9 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     UM_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
     UM_CUDA(launch_umma(S->near, S, bf(S->xhi), bf(S->xlo), ldpx, nrhs, y, ldy, 0, h->s_aux));
     UM_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
-    UM_CUDA(launch_phase_mrhs_f32(h->upleaf, mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
+    UM_CUDA(launch_phase_mrhs_f32(h->upleaf, mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
     for (int l = h->nlev - 1; l >= 0; --l)
-        UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
+        UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
     {
         dim3 g(std::min(64, (S->nc + 255) / 256), nrhs);
         split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_csrc, S->d_cdst, S->nc, nrhs, bf(S->chi), bf(S->clo), ldpc);
@@ -770,9 +770,9 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     }
     UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), ldpc, nrhs, coef, ldc, 0, st));
     for (int l = 0; l < h->nlev; ++l)
-        UM_CUDA(launch_phase_mrhs_f32(h->down[l], mat, segs, x, ldx, coef, ldc, coef, ldc, nrhs, 1, st));
+        UM_CUDA(launch_phase_mrhs_f32(h->down[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 1, st));
     UM_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
-    UM_CUDA(launch_phase_mrhs_f32(h->leafexp, mat, segs, x, ldx, coef, ldc, y, ldy, nrhs, 1, st));
+    UM_CUDA(launch_phase_mrhs_f32(h->leafexp, mat, x, ldx, coef, ldc, y, ldy, nrhs, 1, st));
     return H2_OK;
 }
 

@@ -56,7 +56,7 @@ class _SolveOpts(ctypes.Structure):
 
 class _SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("rel_res", ctypes.c_double),
-                ("status", ctypes.c_int32), ("precond_cycles", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("precond_cycles", ctypes.c_int32), ("reorth_steps", ctypes.c_int32)]
 
 
 class H2Error(RuntimeError):
@@ -316,8 +316,8 @@ class H2Matrix:
         st = torch.cuda.current_stream(B.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres_batched(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), nrhs,
                                         ld, ctypes.byref(opts), PREC[prec], infos, ctypes.c_void_p(st))
-        out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status}
-               for i in infos]
+        out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status,
+                "reorth_steps": i.reorth_steps} for i in infos]
         if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
             _check(status, "h2_gmres_batched")
         return X, out
@@ -349,7 +349,7 @@ class H2Matrix:
         status = lib().h2_gmres(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ld,
                                 ctypes.byref(opts), infos, ctypes.c_void_p(st))
         out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status,
-                "precond_cycles": i.precond_cycles} for i in infos]
+                "precond_cycles": i.precond_cycles, "reorth_steps": i.reorth_steps} for i in infos]
         if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
             _check(status, "h2_gmres")
         return x, out

@@ -51,7 +51,12 @@ typedef enum {
     H2_PREC_FP32 = 0,      /* c64 vectors, FP32 products and accumulation */
     H2_PREC_SPLITBF16 = 1, /* c64 vectors; multi-RHS products on tensor cores
                               with operands split into two bf16 terms */
-    H2_PREC_FP64ACC = 2    /* c128 vectors, stored FP32 data, FP64 accumulation */
+    H2_PREC_FP64ACC = 2,   /* c128 vectors, stored FP32 data, FP64 accumulation */
+    H2_PREC_DFACC = 3      /* c128 vectors, stored FP32 data, double-float
+                              accumulation on the FP32 pipes (each product
+                              split exactly, compensated sums, FP64 reductions
+                              of the per-thread sums); about ten times the
+                              FP64ACC throughput on GB300 */
 } h2_prec;
 
 typedef struct h2_handle h2_handle;
@@ -125,7 +130,7 @@ void h2_free(h2_handle *h);
  * with the inadmissible blocks. x and y are device arrays of nrhs columns of
  * length N with leading dimension ld >= N (elements); y is overwritten and
  * must not overlap x. Element type: c64 for H2_PREC_FP32 / H2_PREC_SPLITBF16,
- * c128 for H2_PREC_FP64ACC. nrhs >= 1.
+ * c128 for H2_PREC_FP64ACC / H2_PREC_DFACC. nrhs >= 1.
  * Paths: nrhs = 1 FP32 runs level-batched GEMVs; nrhs > 1 FP32 runs complex
  * GEMMs on CUDA cores; H2_PREC_SPLITBF16 runs the near-field and coupling
  * products on the tensor cores (tcgen05, operands split into two bf16 terms,
@@ -221,6 +226,13 @@ typedef struct {
                           reduces the true residual by less than 5% turns the
                           preconditioner off for the rest of the solve (plain
                           GMRES is the fallback). */
+    int32_t arnoldi;   /* arithmetic of the Gram-Schmidt passes: 0 = FP64;
+                          1 = double-float (each value an unevaluated sum of two
+                          floats, 48-bit significand; exact product splitting
+                          and compensated sums, Ogita-Rump-Oishi 2005) on the
+                          FP32 pipes, with FP64 reductions, norms and least
+                          squares. GB300 issues FP64 at about 1/58 of the FP32
+                          rate. 1 is not available with precond = 1. */
 } h2_solve_opts;
 
 /* Per right-hand-side outcome of h2_gmres. */

@@ -592,8 +592,9 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out)
 
 // ---- products -------------------------------------------------------------------------
 
+// df: c128 product accumulated in double-float (H2_PREC_DFACC) instead of FP64
 template <typename VT>
-static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st)
+static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st, bool df = false)
 {
     VT *coef = reinterpret_cast<VT *>(h->d_coef);
     const float2 *mat = h->d_mat;
@@ -602,7 +603,8 @@ static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st)
         if constexpr (std::is_same<VT, float2>::value)
             return launch_phase_f32(ph, mat, segs, in0, coef, outp, beta, s);
         else
-            return launch_phase_f64(ph, mat, segs, in0, coef, outp, beta, s);
+            return df ? launch_phase_df(ph, mat, segs, in0, coef, outp, beta, s)
+                      : launch_phase_f64(ph, mat, segs, in0, coef, outp, beta, s);
     };
     H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(VT) * 2 * std::max<int64_t>(1, h->ktot), st));
     H2_CUDA(cudaEventRecord(h->ev_fork, st));
@@ -673,7 +675,7 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
     if (nrhs < 1) return arg_error("h2_matvec: nrhs must be >= 1");
     if (nrhs > 1 && ld < h->n) return arg_error("h2_matvec: ld < n");
     if (x == y) return arg_error("h2_matvec: x and y must not overlap");
-    if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC && prec != H2_PREC_SPLITBF16)
+    if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC && prec != H2_PREC_SPLITBF16 && prec != H2_PREC_DFACC)
         return arg_error("h2_matvec: bad precision");
     H2_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -691,7 +693,7 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
                                    reinterpret_cast<float2 *>(y) + (int64_t)r * ld, st);
         else
             s = run_single<double2>(h, reinterpret_cast<const double2 *>(x) + (int64_t)r * ld,
-                                    reinterpret_cast<double2 *>(y) + (int64_t)r * ld, st);
+                                    reinterpret_cast<double2 *>(y) + (int64_t)r * ld, st, prec == H2_PREC_DFACC);
         if (s != H2_OK) return s;
     }
     return H2_OK;
@@ -704,7 +706,7 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host, int32_t
     if (nrhs < 1) return arg_error("h2_matvec_host: nrhs must be >= 1");
     if (nrhs == 1) ld = h->n;
     if (ld < h->n) return arg_error("h2_matvec_host: ld < n");
-    const size_t esz = prec == H2_PREC_FP64ACC ? sizeof(double2) : sizeof(float2);
+    const size_t esz = (prec == H2_PREC_FP64ACC || prec == H2_PREC_DFACC) ? sizeof(double2) : sizeof(float2);
     const int64_t bytes = (int64_t)esz * ld * nrhs;
     H2_CUDA(cudaSetDevice(h->device));
     if (bytes > h->buf_bytes) {

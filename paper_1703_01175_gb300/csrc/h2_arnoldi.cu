@@ -30,6 +30,7 @@
 #include <complex>
 #include <string>
 
+#include "h2_df.cuh"
 #include "h2_internal.h"
 
 namespace h2 {
@@ -317,6 +318,198 @@ __global__ void arn_to_c128(const float2 *__restrict__ a, double2 *__restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float variant. GB300's FP64 pipe issues about 1/58 of the FP32 rate,
+// so the O(j n) passes can instead carry every value as an unevaluated sum
+// hi + lo of two floats (a 48-bit significand) and run on the FP32 pipes:
+// products are split exactly (TwoProd with an FMA), running sums keep their
+// rounding error in a second float (TwoSum, Knuth), i.e. the compensated dot
+// product of Ogita, Rump & Oishi (2005). Per-thread results are converted to
+// FP64 before any cross-thread reduction, so reductions, norms and the
+// least-squares solve stay in FP64. Basis and work vectors are stored as
+// float4 (re hi, im hi, re lo, im lo): the same 16 bytes per entry as c128.
+// All df arithmetic uses the _rn intrinsics, which are never contracted.
+
+__device__ __forceinline__ float4 df_pack(double2 v)
+{
+    const float2 a = d_to_df(v.x), b = d_to_df(v.y);
+    return make_float4(a.x, b.x, a.y, b.y);
+}
+
+__device__ __forceinline__ float4 ldcs4(const float4 *p) { return __ldcs(p); }
+
+// conj(v) w into (sr, cr) + i (si, ci)
+__device__ __forceinline__ void df_cmac_conj(float *a, float4 v, float4 w)
+{
+    df_mac(a[0], a[1], v.x, v.z, w.x, w.z);
+    df_mac(a[0], a[1], v.y, v.w, w.y, w.w);
+    df_mac(a[2], a[3], v.x, v.z, w.y, w.w);
+    df_mac(a[2], a[3], -v.y, -v.w, w.x, w.z);
+}
+
+// acc -= v h
+__device__ __forceinline__ void df_cmsub(float *a, float4 v, float4 h)
+{
+    df_mac(a[0], a[1], -v.x, -v.z, h.x, h.z);
+    df_mac(a[0], a[1], v.y, v.w, h.y, h.w);
+    df_mac(a[2], a[3], -v.x, -v.z, h.y, h.w);
+    df_mac(a[2], a[3], -v.y, -v.w, h.x, h.z);
+}
+
+// w = y32 (exact in double-float)
+__global__ void arn_widen_df(ArnDev K, const float2 *__restrict__ y32)
+{
+    const int r = blockIdx.y;
+    const float2 *y = y32 + (size_t)r * K.n;
+    float4 *w = reinterpret_cast<float4 *>(K.w) + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x)
+        w[i] = make_float4(y[i].x, y[i].y, 0.f, 0.f);
+}
+
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_dot_df(ArnDev K, int j, int S, int seg)
+{
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const int l = blockIdx.x / S, s = blockIdx.x - l * S;
+    const int i0 = s * seg, i1 = min(K.n, i0 + seg);
+    const float4 *w = reinterpret_cast<const float4 *>(K.w) + (size_t)r * K.n;
+    float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+    if (l <= j) {
+        const float4 *Vl = reinterpret_cast<const float4 *>(K.V) + ((size_t)l * K.R + r) * K.n;
+        int i = i0 + threadIdx.x;
+        for (; i + AT < i1; i += 2 * AT) {
+            df_cmac_conj(a0, ldcs4(Vl + i), w[i]);
+            df_cmac_conj(a1, ldcs4(Vl + i + AT), w[i + AT]);
+        }
+        if (i < i1) df_cmac_conj(a0, ldcs4(Vl + i), w[i]);
+    } else {  // FIRST only: |w|^2 over the segment
+        for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+            const float4 v = w[i];
+            df_mac(a0[0], a0[1], v.x, v.z, v.x, v.z);
+            df_mac(a0[0], a0[1], v.y, v.w, v.y, v.w);
+        }
+    }
+    const double2 mine = make_double2(df_to_d(a0[0], a0[1]) + df_to_d(a1[0], a1[1]),
+                                      df_to_d(a0[2], a0[3]) + df_to_d(a1[2], a1[3]));
+    const double2 tot = block_sum(mine);
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 2 : 0))) return;
+    const int ncols = SECOND ? j + 1 : j + 2;
+    reduce_columns(part, ncols, S, (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2));
+}
+
+// Dynamic shared memory: m + 2 float4 entries.
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_update_df(ArnDev K, int j, int rows)
+{
+    extern __shared__ float4 hsf[];
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const double2 *h = (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2);
+    for (int l = threadIdx.x; l <= j; l += AT) hsf[l] = df_pack(h[l]);
+    __syncthreads();
+    const int i0 = blockIdx.x * rows, i1 = min(K.n, i0 + rows);
+    float4 *w = reinterpret_cast<float4 *>(K.w) + (size_t)r * K.n;
+    const float4 *V = reinterpret_cast<const float4 *>(K.V) + (size_t)r * K.n;
+    const size_t ldv = (size_t)K.R * K.n;
+    double nrm = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+        const float4 w0 = w[i];
+        float a[4] = {w0.x, w0.z, w0.y, w0.w};
+        int l = 0;
+        for (; l + 1 <= j; l += 2) {
+            const float4 va = ldcs4(V + (size_t)l * ldv + i), vb = ldcs4(V + (size_t)(l + 1) * ldv + i);
+            df_cmsub(a, va, hsf[l]);
+            df_cmsub(a, vb, hsf[l + 1]);
+        }
+        if (l <= j) df_cmsub(a, ldcs4(V + (size_t)l * ldv + i), hsf[l]);
+        const float2 re = df_norm(a[0], a[1]), im = df_norm(a[2], a[3]);
+        w[i] = make_float4(re.x, im.x, re.y, im.y);
+        const double dr = df_to_d(re.x, re.y), di = df_to_d(im.x, im.y);
+        nrm = fma(dr, dr, nrm);
+        nrm = fma(di, di, nrm);
+    }
+    const double2 tot = block_sum(make_double2(nrm, 0.0));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 3 : 1))) return;
+    double s = 0.0;
+    const volatile double2 *p = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += AT) s += p[b].x;
+    const double nw2 = block_sum(make_double2(s, 0.0)).x;
+    if (threadIdx.x != 0) return;
+    if (!SECOND) {
+        const double rho = K.h1[(size_t)r * (K.m + 2) + j + 1].x;
+        const bool again = !(nw2 >= REORTH2 * rho);
+        K.scal[8 * r + 3] = again ? 1.0 : 0.0;
+        if (again) return;
+    }
+    K.scal[8 * r] = sqrt(nw2);
+}
+
+// v_{jn} = w / beta in double-float; x32 = its high part
+__global__ void arn_normalize_df(ArnDev K, int jn, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const float2 inv = d_to_df(beta > 0.0 ? 1.0 / beta : 0.0);
+    float4 *Vn = reinterpret_cast<float4 *>(K.V) + ((size_t)jn * K.R + r) * K.n;
+    const float4 *w = reinterpret_cast<const float4 *>(K.w) + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const float4 v = w[i];
+        float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+        df_mac(sr, cr, v.x, v.z, inv.x, inv.y);
+        df_mac(si, ci, v.y, v.w, inv.x, inv.y);
+        const float2 re = df_norm(sr, cr), im = df_norm(si, ci);
+        Vn[i] = make_float4(re.x, im.x, re.y, im.y);
+        x[i] = make_float2(re.x, im.x);
+    }
+}
+
+// v_0 = rr / beta
+__global__ void arn_start_df(ArnDev K, const double2 *__restrict__ rr, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    float4 *V0 = reinterpret_cast<float4 *>(K.V) + (size_t)r * K.n;
+    const double2 *v = rr + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const float4 q = df_pack(make_double2(v[i].x * inv, v[i].y * inv));
+        V0[i] = q;
+        x[i] = make_float2(q.x, q.y);
+    }
+}
+
+// x += V y (c128 x; df basis); dynamic shared memory: m + 2 float4 entries
+__global__ void arn_xupdate_df(ArnDev K, double2 *__restrict__ x, int64_t ldx)
+{
+    extern __shared__ float4 ysf[];
+    const int r = blockIdx.y;
+    const int k = K.kact[r];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) ysf[l] = df_pack(K.h1[(size_t)r * (K.m + 2) + l]);
+    __syncthreads();
+    if (k == 0) return;
+    const size_t ldb = (size_t)K.R * K.n;
+    const float4 *V = reinterpret_cast<const float4 *>(K.V) + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const float4 x0 = df_pack(x[(size_t)r * ldx + i]);
+        float a[4] = {x0.x, x0.z, x0.y, x0.w};
+        for (int l = 0; l < k; ++l) {
+            const float4 v = V[(size_t)l * ldb + i], y = ysf[l];
+            df_mac(a[0], a[1], v.x, v.z, y.x, y.z);
+            df_mac(a[0], a[1], -v.y, -v.w, y.y, y.w);
+            df_mac(a[2], a[3], v.x, v.z, y.y, y.w);
+            df_mac(a[2], a[3], v.y, v.w, y.x, y.z);
+        }
+        x[(size_t)r * ldx + i] = make_double2(df_to_d(a[0], a[1]), df_to_d(a[2], a[3]));
+    }
+}
+
 // segments of the dot pass at step j: enough blocks to fill the GPU
 void dot_split(int n, int R, int j, int *S, int *seg)
 {
@@ -350,17 +543,20 @@ void arn_free(ArnWork *w)
     delete w;
 }
 
-h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols)
+h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
 {
     ArnWork *w = *slot;
-    if (w && w->n == n && w->m == m && w->R == R && w->extra_cols == extra_cols) return H2_OK;
+    if (w && w->n == n && w->m == m && w->R == R && w->extra_cols == extra_cols && w->mode == mode) return H2_OK;
     arn_free(w);
     *slot = nullptr;
+    if (mode != ARN_FP64 && mode != ARN_DF) return (set_error("GMRES: unknown Arnoldi arithmetic"), H2_ERR_ARG);
+    if (mode == ARN_DF && extra_cols) return (set_error("GMRES: double-float Arnoldi has no flexible variant"), H2_ERR_ARG);
     w = new ArnWork();
     w->n = n;
     w->m = m;
     w->R = R;
     w->extra_cols = extra_cols;
+    w->mode = mode;
     // update / residual grid: rows per block, multiple of 32
     int nb = std::max(1, std::min((n + AT - 1) / AT, (TARGET + R - 1) / R));
     int rows = (n + nb - 1) / nb;
@@ -423,14 +619,7 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols)
         arn_free(w);
         return H2_ERR_CUDA;
     }
-    const int smem = (int)(sizeof(double2) * (m + 2));
-    if (cudaFuncSetAttribute(arn_update<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(arn_update<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
-        cudaFuncSetAttribute(arn_xupdate, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-        arn_free(w);
-        set_error("GMRES: shared-memory attribute rejected");
-        return H2_ERR_CUDA;
-    }
+    // dynamic shared memory of the update kernels: (m + 2) x 16 bytes <= 16.4 KB, under the default limit
     w->H.assign((size_t)R * m * (m + 1), 0.0);
     w->g.assign((size_t)R * (m + 1), 0.0);
     w->sn.assign((size_t)R * m, 0.0);
@@ -454,7 +643,10 @@ h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 
 
 h2_status arn_start(ArnWork *w, cudaStream_t st)
 {
-    arn_start<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
+    if (w->mode == ARN_DF)
+        arn_start_df<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
+    else
+        arn_start<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
     ARNC(cudaGetLastError());
     const int m = w->m;
     for (int r = 0; r < w->R; ++r) {
@@ -523,12 +715,22 @@ h2_status arn_step(ArnWork *w, int j, cudaStream_t st)
     int S, seg;
     dot_split(w->n, w->R, j, &S, &seg);
     const size_t smem = sizeof(double2) * (w->m + 2);
-    arn_widen<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
-    arn_dot<false><<<dim3((j + 2) * S, w->R), AT, 0, st>>>(K, j, S, seg);
-    arn_update<false><<<dim3(w->nbu, w->R), AT, smem, st>>>(K, j, w->rows);
-    arn_dot<true><<<dim3((j + 1) * S, w->R), AT, 0, st>>>(K, j, S, seg);
-    arn_update<true><<<dim3(w->nbu, w->R), AT, smem, st>>>(K, j, w->rows);
-    arn_normalize<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+    const dim3 g1((j + 2) * S, w->R), g2((j + 1) * S, w->R), gu(w->nbu, w->R);
+    if (w->mode == ARN_DF) {
+        arn_widen_df<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
+        arn_dot_df<false><<<g1, AT, 0, st>>>(K, j, S, seg);
+        arn_update_df<false><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_dot_df<true><<<g2, AT, 0, st>>>(K, j, S, seg);
+        arn_update_df<true><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_normalize_df<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+    } else {
+        arn_widen<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
+        arn_dot<false><<<g1, AT, 0, st>>>(K, j, S, seg);
+        arn_update<false><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_dot<true><<<g2, AT, 0, st>>>(K, j, S, seg);
+        arn_update<true><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_normalize<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+    }
     ARNC(cudaGetLastError());
     ARNC(cudaMemcpyAsync(w->h_hh, K.h1, sizeof(double2) * 2 * w->R * (w->m + 2), cudaMemcpyDeviceToHost, st));
     ARNC(cudaMemcpyAsync(w->h_scal, K.scal, 8 * sizeof(double) * w->R, cudaMemcpyDeviceToHost, st));
@@ -563,7 +765,10 @@ h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, 
     }
     ARNC(cudaMemcpyAsync(w->K.h1, w->h_hh, sizeof(double2) * w->R * (m + 2), cudaMemcpyHostToDevice, st));
     ARNC(cudaMemcpyAsync(w->K.kact, w->h_kact, sizeof(int) * w->R, cudaMemcpyHostToDevice, st));
-    arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
+    if (w->mode == ARN_DF)
+        arn_xupdate_df<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, x, ldx);
+    else
+        arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
     ARNC(cudaGetLastError());
     return H2_OK;
 }

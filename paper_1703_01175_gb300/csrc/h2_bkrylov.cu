@@ -29,8 +29,9 @@ static h2_status bk_true_residual(h2_handle *h, ArnWork *w, const double2 *b, in
     const int n = h->n, R = w->R;
     h2_status s;
     if (refine) {
+        const h2_prec acc = w->mode == ARN_DF ? H2_PREC_DFACC : H2_PREC_FP64ACC;
         for (int r = 0; r < R; ++r)
-            if ((s = h2_matvec(h, x + (size_t)r * ldx, w->tmp + (size_t)r * n, 1, n, H2_PREC_FP64ACC, st)) != H2_OK)
+            if ((s = h2_matvec(h, x + (size_t)r * ldx, w->tmp + (size_t)r * n, 1, n, acc, st)) != H2_OK)
                 return s;
     } else {
         if ((s = arn_c128_to_c64(w, x, ldx, w->x32, st)) != H2_OK) return s;
@@ -53,7 +54,7 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
     if (cudaSetDevice(h->device) != cudaSuccess) return (set_error("h2_gmres_batched: cudaSetDevice failed"), H2_ERR_CUDA);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ArnWork *w = reinterpret_cast<ArnWork *>(h->bkrylov);
-    h2_status s = arn_get(&w, h->n, m, nrhs, 0);
+    h2_status s = arn_get(&w, h->n, m, nrhs, 0, opts->arnoldi);
     h->bkrylov = w;
     if (s != H2_OK) return s;
     const int n = h->n, R = nrhs;

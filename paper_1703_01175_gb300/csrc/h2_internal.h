@@ -92,8 +92,8 @@ void set_error(const std::string &msg);
 
 // FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
 struct ArnDev {
-    double2 *V;        // basis [(m+1)][R][n]
-    double2 *w;        // [R][n] vector being orthogonalised
+    double2 *V;        // basis [(m+1)][R][n] (float4 hi/lo pairs in double-float mode)
+    double2 *w;        // [R][n] vector being orthogonalised (likewise)
     double2 *part;     // [R][np] partial sums of the reductions
     unsigned *ticket;  // [R][8] last-block counters
     double2 *h1, *h2;  // [R][m+2] projection coefficients (h1[j+1] = |w|^2); h2 follows h1
@@ -102,9 +102,11 @@ struct ArnDev {
     int n, m, R, np;
 };
 
+enum { ARN_FP64 = 0, ARN_DF = 1 };  // Arnoldi arithmetic: FP64, or double-float on the FP32 pipes
+
 struct ArnWork {
     ArnDev K{};
-    int n = 0, m = 0, R = 0, extra_cols = 0;
+    int n = 0, m = 0, R = 0, extra_cols = 0, mode = ARN_FP64;
     int rows = 0, nbu = 0;          // row blocks of the update and residual passes
     double2 *Z = nullptr;           // [extra_cols][R][n] preconditioned directions (flexible GMRES)
     double2 *rr = nullptr, *tmp = nullptr;  // [R][n]
@@ -120,7 +122,7 @@ struct ArnWork {
     std::vector<char> bad, reorth;               // after a step: non-finite, second projection taken
 };
 
-h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols);
+h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode);
 void arn_free(ArnWork *w);
 // rr = b - y (y NULL: rr = b); scal[8 r] = |rr_r|
 h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st);
@@ -211,6 +213,9 @@ cudaError_t launch_phase_mrhs_f32(const Phase &ph, const float2 *mat, const floa
                                   const float2 *in1, int64_t ld1, float2 *out, int64_t ldo, int nrhs, int beta_one,
                                   cudaStream_t st);
 cudaError_t launch_phase_f64(const Phase &ph, const float2 *mat, const Seg *segs,
+                             const double2 *in0, const double2 *in1, double2 *out,
+                             int beta_one, cudaStream_t st);
+cudaError_t launch_phase_df(const Phase &ph, const float2 *mat, const Seg *segs,
                              const double2 *in0, const double2 *in1, double2 *out,
                              int beta_one, cudaStream_t st);
 }  // namespace h2

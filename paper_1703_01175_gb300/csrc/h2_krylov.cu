@@ -34,7 +34,8 @@ static h2_status true_residual(h2_handle *h, ArnWork *w, const double2 *b, const
     if (x_zero) return arn_residual(w, b, n, nullptr, st);
     h2_status s;
     if (refine) {
-        if ((s = h2_matvec(h, x, w->tmp, 1, n, H2_PREC_FP64ACC, st)) != H2_OK) return s;
+        const h2_prec acc = w->mode == ARN_DF ? H2_PREC_DFACC : H2_PREC_FP64ACC;
+        if ((s = h2_matvec(h, x, w->tmp, 1, n, acc, st)) != H2_OK) return s;
     } else {
         if ((s = arn_c128_to_c64(w, x, n, w->x32, st)) != H2_OK) return s;
         if ((s = h2_matvec(h, w->x32, w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
@@ -59,7 +60,7 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
     if (cudaSetDevice(h->device) != cudaSuccess) return (set_error("h2_gmres: cudaSetDevice failed"), H2_ERR_CUDA);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ArnWork *w = reinterpret_cast<ArnWork *>(h->krylov);
-    h2_status s = arn_get(&w, h->n, m, 1, flexible ? m : 0);
+    h2_status s = arn_get(&w, h->n, m, 1, flexible ? m : 0, opts->arnoldi);
     h->krylov = w;
     if (s != H2_OK) return s;
     const int n = h->n;

@@ -9,7 +9,8 @@
 // rows are staged in shared memory per stage by asynchronous copies, NSTG
 // stages in flight. Warp w owns rows 4w..4w+3 of the tile and lane l the
 // right-hand sides l, l+32, ..., so a thread accumulates 4 x RPT complex
-// outputs and writes 32 contiguous bytes per right-hand side. The input index
+// outputs; the finished tile is transposed in shared memory so that the
+// stores (and the reads of beta = 1) are 256-byte runs. The input index
 // of every task column comes from a table built once (h2_ensure_colidx).
 // Vectors are column-major with a leading dimension per buffer (x: ld0,
 // coefficients: ld1, y: ldo).
@@ -44,7 +45,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-constexpr size_t gemm_smem_bytes(int rpt) { return sizeof(float2) * NSTG * KB * (MR + 32 * rpt + 1); }
+constexpr size_t gemm_smem_bytes(int rpt)
+{
+    const size_t pipe = sizeof(float2) * NSTG * KB * (MR + 32 * rpt + 1);
+    const size_t tile = sizeof(float2) * 32 * rpt * (MR + 1);
+    return pipe > tile ? pipe : tile;
+}
 
 template <int RPT>
 __global__ void __launch_bounds__(GT, 2)
@@ -137,21 +143,31 @@ rowgemm_f32_kernel(const Task *__restrict__ tasks, const int32_t *__restrict__ c
         }
     }
     cp_async_wait<0>();
+    __syncthreads();
+    // Epilogue through shared memory: the tile is transposed so that each warp
+    // writes (and, with beta_one, reads) 32 consecutive rows of one right-hand
+    // side, i.e. 256 contiguous bytes, instead of one scattered 32-byte run
+    // per lane.
+    constexpr int TS = MR + 1;  // odd stride: conflict-free transposition
+    float2 *T = gsm;            // [NR][TS], fits in the pipeline buffers
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        const int rr = r0 + lane + 32 * q;
-        if (rr >= nrhs) continue;
-        float2 *o = out + (int64_t)rr * ldo + tk.out_off + row0 + rg * 4;
+    for (int q = 0; q < RPT; ++q)
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            if (row0 + rg * 4 + p >= tk.m) break;
-            float2 v = make_float2(acc[p][q][0], acc[p][q][1]);
+        for (int p = 0; p < 4; ++p) T[(lane + 32 * q) * TS + rg * 4 + p] = make_float2(acc[p][q][0], acc[p][q][1]);
+    __syncthreads();
+    const int row = row0 + lane;
+    if (row < tk.m) {
+        for (int rl = rg; rl < NR; rl += GT / 32) {
+            const int rr = r0 + rl;
+            if (rr >= nrhs) break;
+            float2 *o = out + (int64_t)rr * ldo + tk.out_off + row;
+            float2 v = T[rl * TS + lane];
             if (beta_one) {
-                const float2 pv = o[p];
+                const float2 pv = *o;
                 v.x += pv.x;
                 v.y += pv.y;
             }
-            o[p] = v;
+            *o = v;
         }
     }
 }

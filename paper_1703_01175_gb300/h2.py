@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libh2.so")
 H2_OK, H2_ERR_ARG, H2_ERR_ALLOC, H2_ERR_CUDA = 0, 1, 2, 3
 H2_ERR_NOT_CONVERGED, H2_ERR_BREAKDOWN, H2_ERR_TIMEOUT, H2_ERR_STATE = 4, 5, 6, 7
 H2_C64, H2_C128 = 0, 1
-PREC = {"fp32": 0, "splitbf16": 1, "fp64acc": 2}
+PREC = {"fp32": 0, "splitbf16": 1, "fp64acc": 2, "dfacc": 3}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -49,9 +49,14 @@ class _Stats(ctypes.Structure):
         ("max_rank", ctypes.c_int32), ("kernels_per_matvec", ctypes.c_int32)]
 
 
+# arithmetic of the Gram-Schmidt passes: FP64, or double-float on the FP32 pipes
+ARNOLDI = {"fp64": 0, "df": 1}
+
+
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
-                ("refine", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("refine", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("arnoldi", ctypes.c_int32)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -263,10 +268,10 @@ class H2Matrix:
 
     def matvec(self, x, y=None, prec: str = "fp32", stream=None):
         """y = A x on the device. x: torch complex64 (fp32, splitbf16) or
-        complex128 (fp64acc) CUDA tensor of shape (n,) or (n, nrhs) column-major
+        complex128 (fp64acc, dfacc) CUDA tensor of shape (n,) or (n, nrhs) column-major
         (i.e. x.t() contiguous) or (nrhs, n) contiguous rows via x.T."""
         import torch
-        want = torch.complex128 if prec == "fp64acc" else torch.complex64
+        want = torch.complex128 if prec in ("fp64acc", "dfacc") else torch.complex64
         if x.dtype != want or not x.is_cuda:
             raise TypeError(f"x must be a CUDA {want} tensor")
         nrhs, ld = self._shape(x)
@@ -291,7 +296,7 @@ class H2Matrix:
 
     def matvec_host(self, x: np.ndarray, prec: str = "fp32") -> np.ndarray:
         """y = A x with host numpy arrays (copies inside the call)."""
-        want = np.complex128 if prec == "fp64acc" else np.complex64
+        want = np.complex128 if prec in ("fp64acc", "dfacc") else np.complex64
         x = np.asarray(x)
         if x.dtype != want:
             raise TypeError(f"x must be {want}")
@@ -303,7 +308,7 @@ class H2Matrix:
         return y
 
     def gmres_batched(self, B, X=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
-                      prec="splitbf16", stream=None, check=True):
+                      prec="splitbf16", arnoldi="fp64", stream=None, check=True):
         """Batched GMRES for B (n, nrhs) column-major complex128 on the device."""
         import torch
         if B.dtype != torch.complex128 or not B.is_cuda:
@@ -311,7 +316,8 @@ class H2Matrix:
         nrhs, ld = self._shape(B)
         if X is None:
             X = torch.zeros_like(B)
-        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), 0)
+        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), 0,
+                          ARNOLDI[arnoldi])
         infos = (_SolveInfo * nrhs)()
         st = torch.cuda.current_stream(B.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres_batched(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), nrhs,
@@ -334,7 +340,7 @@ class H2Matrix:
         return lib().h2_device_status(self._h)
 
     def gmres(self, b, x=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
-              precond=0, stream=None, check=True):
+              precond=0, arnoldi="fp64", stream=None, check=True):
         """Solve A x = b on the device. b: CUDA complex128 (n,) or (n, nrhs)
         column-major. Returns (x, [info dict per RHS])."""
         import torch
@@ -343,7 +349,8 @@ class H2Matrix:
         nrhs, ld = self._shape(b)
         if x is None:
             x = torch.zeros_like(b)
-        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), int(precond))
+        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), int(precond),
+                          ARNOLDI[arnoldi])
         infos = (_SolveInfo * nrhs)()
         st = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ld,

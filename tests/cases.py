@@ -43,6 +43,19 @@ class Case:
             return h2mv.h2_matvec(self.hZ, x)
         return np.stack([h2mv.h2_matvec(self.hZ, x[:, j]) for j in range(x.shape[1])], axis=1)
 
+    @functools.cached_property
+    def hZ32(self):
+        """The same H^2 data rounded to complex64, as the device stores it."""
+        def rnd(d):
+            return None if d is None else {k: v.astype(np.complex64).astype(np.complex128) for k, v in d.items()}
+        h = self.hZ
+        return h2build.H2(h.tree, h.part, h.rank, rnd(h.U), rnd(h.W), rnd(h.T), rnd(h.S), rnd(h.Z))
+
+    def oracle_matvec_stored(self, x):
+        """FP64 product with the complex64-rounded data: the exact result an
+        accumulation of the stored data should reproduce."""
+        return h2mv.h2_matvec(self.hZ32, x)
+
 
 @functools.lru_cache(maxsize=None)
 def get(name: str) -> Case:

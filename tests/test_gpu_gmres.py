@@ -83,15 +83,36 @@ def test_gmres_initial_guess(mats):
     assert torch.allclose(x, x2)
 
 
+@pytest.mark.parametrize("refine", [True, False])
+def test_gmres_double_float_arnoldi(mats, refine):
+    """Double-float Gram-Schmidt on the FP32 pipes: same convergence as the
+    FP64 one and an oracle residual within the tolerance."""
+    c = cases.get("cube8")
+    w = synth.workload("cube8")
+    b = synth.default_rhs(w)[c.tree.unknown_perm()]
+    tol = 1e-6 if refine else 1e-5
+    bt = torch.from_numpy(b).cuda()
+    x1, i1 = mats["cube8"].gmres(bt, tol=tol, restart=50, refine=refine)
+    x2, i2 = mats["cube8"].gmres(bt, tol=tol, restart=50, refine=refine, arnoldi="df")
+    assert i2[0]["status"] == 0, i2
+    assert abs(i1[0]["iterations"] - i2[0]["iterations"]) <= 1
+    x2 = x2.cpu().numpy()
+    assert _oracle_res(c, x2, b) <= tol * (1.0 if refine else 1.05) + 2e-7
+    xo, it, hist = krylov.gmres(c.oracle_matvec, b, tol, restart=50)
+    assert np.linalg.norm(x2 - xo) <= 50 * tol * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("arnoldi", ["fp64", "df"])
 @pytest.mark.parametrize("prec", ["splitbf16", "fp32"])
-def test_batched_gmres_matches_oracle(mats, prec):
+def test_batched_gmres_matches_oracle(mats, prec, arnoldi):
     """Batched GMRES (one multi-RHS product per Arnoldi step): every column's
     oracle FP64 residual within the tolerance."""
     c = cases.get("cube12")
     R = 5
     B = np.asfortranarray(synth.random_complex(c.n, 17, cols=R))
     Bt = torch.from_numpy(B).cuda().t().contiguous().t()
-    X, info = mats["cube12"].gmres_batched(Bt, tol=1e-4, restart=30, maxit=2000, refine=True, prec=prec)
+    X, info = mats["cube12"].gmres_batched(Bt, tol=1e-4, restart=30, maxit=2000, refine=True, prec=prec,
+                                           arnoldi=arnoldi)
     X = X.cpu().numpy()
     for j in range(R):
         assert info[j]["status"] == 0, info[j]

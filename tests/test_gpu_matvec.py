@@ -64,6 +64,19 @@ def test_fp64acc_matches_oracle(loaded, name):
     assert _rel(y, y_or) <= 1e-6
 
 
+@pytest.mark.parametrize("prec", ["fp64acc", "dfacc"])
+@pytest.mark.parametrize("name", ["cube8", "cube12"])
+def test_accumulation_exact_on_stored_data(loaded, name, prec):
+    """FP64 and double-float accumulation reproduce the FP64 product of the
+    FP32-stored data to 1e-12 (FP32 accumulation would be off by ~1e-7)."""
+    c = cases.get(name)
+    A = _mat(loaded, name)
+    x = synth.random_complex(c.n, 5)
+    y_ex = c.oracle_matvec_stored(x)
+    y = A.matvec(torch.from_numpy(x).cuda(), prec=prec).cpu().numpy()
+    assert _rel(y, y_ex) <= 1e-12
+
+
 def test_c64_input_and_symmetric_form(loaded):
     c = cases.get("cube8")
     x = synth.random_complex(c.n, 4)

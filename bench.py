@@ -308,29 +308,34 @@ def run_ours(args, rank, world, local_rank):
         mr["speedup_vs_single_rhs_fp32"] = (ms * R) / mr["splitbf16"]["ms"]
         mr["tc_entries"] = tc_entries
 
-    # "new" solve: R right-hand sides in lockstep, split-bf16 tensor-core products, FP64 Arnoldi,
-    # FP64-accumulated restart residuals; compared per right-hand side with plain single-RHS GMRES
+    # "new" solve: R right-hand sides in lockstep, split-bf16 tensor-core products, double-float Arnoldi and
+    # double-float-accumulated restart residuals; compared per right-hand side with plain single-RHS GMRES
+    # (FP32 products, FP64 Arnoldi, FP64-accumulated restart residuals)
     if args.gmres_batch > 0:
         R = args.gmres_batch
         Bm = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
         Bt = torch.from_numpy(np.asfortranarray(Bm)).to(dev).t().contiguous().t()
         m_new = args.gmres_restart
-        for label, rst in (("plain_m%d" % m_new, m_new),):
+        b0 = Bt[:, 0].contiguous()
+        for label, arn in (("plain_m%d" % m_new, "fp64"), ("plain_m%d_df" % m_new, "df")):
             torch.cuda.synchronize(dev)
             g0 = torch.cuda.Event(enable_timing=True)
             g1 = torch.cuda.Event(enable_timing=True)
             g0.record(stream)
-            xs, info = A.gmres(Bt[:, 0].contiguous(), tol=w.tol, restart=rst, maxit=4000, refine=True)
+            xs, info = A.gmres(b0, tol=w.tol, restart=m_new, maxit=4000, refine=True, arnoldi=arn)
             g1.record(stream)
             torch.cuda.synchronize(dev)
             gm[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
                          "rel_res": info[0]["rel_res"], "status": info[0]["status"],
-                         "reorth_steps": info[0]["reorth_steps"]}
+                         "reorth_steps": info[0]["reorth_steps"],
+                         "arnoldi": "FP64" if arn == "fp64" else "double-float on the FP32 pipes",
+                         "refinement_product": "FP64ACC" if arn == "fp64" else "DFACC"}
         torch.cuda.synchronize(dev)
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        Xs, info = A.gmres_batched(Bt, tol=w.tol, restart=m_new, maxit=4000, refine=True, prec="splitbf16")
+        Xs, info = A.gmres_batched(Bt, tol=w.tol, restart=m_new, maxit=4000, refine=True, prec="splitbf16",
+                                   arnoldi="df")
         g1.record(stream)
         torch.cuda.synchronize(dev)
         t_new = g0.elapsed_time(g1)
@@ -339,8 +344,9 @@ def run_ours(args, rank, world, local_rank):
                              "max_rel_res": max(i["rel_res"] for i in info),
                              "mean_iterations": float(np.mean([i["iterations"] for i in info])),
                              "mean_reorth_steps": float(np.mean([i["reorth_steps"] for i in info])),
-                             "products": "split-bf16 tensor cores, FP64 Gram-Schmidt with selective "
-                                         "reorthogonalisation, FP64-accumulated restart residuals"}
+                             "products": "split-bf16 tensor cores; double-float Gram-Schmidt (FP32 pipes, FP64 "
+                                         "reductions) with selective reorthogonalisation; double-float-accumulated "
+                                         "restart residuals"}
         gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
 
     # learned preconditioner (shipped weights, trained by train_precond on the 16^3 cube): flexible
@@ -436,6 +442,32 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def fp_rates():
+    """FP64 and FP32 (tensor cores off) GEMM throughput of cuda:0 with cuBLAS:
+    the ceilings of the FP64 Gram-Schmidt passes and of their double-float
+    replacement on the FP32 pipes."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    for name, dt, n in (("fp64", torch.float64, 8192), ("fp32", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(3):
+            torch.matmul(a, b)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3 if dt == torch.float64 else 10
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"n": n, "ms": ms, "tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+    print(json.dumps({"gemm_rates": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,6 +480,8 @@ def main():
     ap.add_argument("--gmres-batch", type=int, default=32, help="right-hand sides of the batched solve (0: skip)")
     ap.add_argument("--gmres-restart", type=int, default=400, help="restart of the batched / plain comparison")
     ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
+    ap.add_argument("--fp-rates", action="store_true",
+                    help="print the FP64 and FP32 (non-tensor) GEMM rates of the GPU and exit")
     ap.add_argument("--mrhs-prec", default="splitbf16", choices=["splitbf16", "fp32"],
                     help="product of the --only-mrhs profiling mode")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")
@@ -456,6 +490,9 @@ def main():
     ap.add_argument("--only-matvec", action="store_true",
                     help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
     args = ap.parse_args()
+    if args.fp_rates:
+        fp_rates()
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

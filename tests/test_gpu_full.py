@@ -4,10 +4,13 @@ the H^2 data of the host constructor, the launch configuration bench.py times.
 - FP32 product vs the oracle's FP64 H^2 product on the same data: 1e-5;
 - sampled rows against the oracle's dense VIE rows, evaluated one by one:
   representation error within 10 eps;
-- GMRES to 1e-4: the oracle's FP64 residual of the GPU solution <= 1.05e-4.
-  This random-permittivity cube is hard for restarted GMRES: with m = 50 the
+- GMRES to 1e-4 (single right-hand side, and the batched double-float solve):
+  the oracle's FP64 residual of each GPU solution <= 1.05e-4. This
+  random-permittivity cube is hard for restarted GMRES: with m = 50 the
   residual stagnates near 7e-4 (the GPU and the oracle agree on that on the
-  smaller 16^3 version), so the solve uses m = 400.
+  smaller 16^3 version), so the solves use m = 400;
+- split-bf16 products of 8 right-hand sides: sampled columns within eps;
+- double-float and FP64 accumulation agree to 1e-12.
 """
 import math
 
@@ -63,3 +66,41 @@ def test_full_size_gmres_residual(full):
     x = x.cpu().numpy()
     res = np.linalg.norm(b - h2mv.h2_matvec(hZ, x)) / np.linalg.norm(b)
     assert res <= 1.05 * w.tol
+
+
+def test_full_size_split_product_sampled_columns(full):
+    """Split-bf16 tensor-core product of 8 right-hand sides at full size:
+    two sampled columns against the oracle's FP64 product, within eps."""
+    w, arrs, perm, A, hZ = full
+    R = 8
+    X = synth.random_complex(arrs.n, 23, cols=R).astype(np.complex64)
+    Xt = torch.from_numpy(np.asfortranarray(X)).cuda().t().contiguous().t()
+    Y = A.matvec(Xt, prec="splitbf16").cpu().numpy()
+    for j in (0, R - 1):
+        y_or = h2mv.h2_matvec(hZ, X[:, j].astype(np.complex128))
+        assert np.linalg.norm(Y[:, j] - y_or) <= w.eps * np.linalg.norm(y_or)
+
+
+def test_full_size_accumulated_products_agree(full):
+    """Double-float and FP64 accumulation of the stored data agree to 1e-12."""
+    w, arrs, perm, A, hZ = full
+    x = torch.from_numpy(synth.random_complex(arrs.n, 24)).cuda()
+    ya = A.matvec(x, prec="fp64acc")
+    yd = A.matvec(x, prec="dfacc")
+    assert float(torch.linalg.norm(ya - yd) / torch.linalg.norm(ya)) <= 1e-12
+
+
+def test_full_size_batched_double_float_gmres(full):
+    """The batched solve bench.py times (split-bf16 products, double-float
+    Arnoldi and restart residuals, m = 400) on 4 plane waves: the oracle's
+    FP64 residual of every solution <= 1.05 tol."""
+    w, arrs, perm, A, hZ = full
+    R = 4
+    B = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
+    Bt = torch.from_numpy(np.asfortranarray(B)).cuda().t().contiguous().t()
+    X, info = A.gmres_batched(Bt, tol=w.tol, restart=400, maxit=3000, refine=True, prec="splitbf16", arnoldi="df")
+    X = X.cpu().numpy()
+    for j in range(R):
+        assert info[j]["status"] == 0, info[j]
+        res = np.linalg.norm(B[:, j] - h2mv.h2_matvec(hZ, X[:, j])) / np.linalg.norm(B[:, j])
+        assert res <= 1.05 * w.tol

@@ -233,6 +233,12 @@ typedef struct {
                           FP32 pipes, with FP64 reductions, norms and least
                           squares. GB300 issues FP64 at about 1/58 of the FP32
                           rate. 1 is not available with precond = 1. */
+    double reorth_eta; /* selective reorthogonalisation threshold eta in [0, 1]:
+                          a second Gram-Schmidt projection when the first
+                          leaves |w'| < eta |w| (Daniel, Gragg, Kaufman &
+                          Stewart 1976); one projection keeps w' orthogonal to
+                          the basis to about u / eta. 0 selects 1/sqrt(2);
+                          1 projects twice at every step (CGS2). */
 } h2_solve_opts;
 
 /* Per right-hand-side outcome of h2_gmres. */

@@ -6,7 +6,9 @@
 // Orthogonalisation is classical Gram-Schmidt with selective
 // reorthogonalisation (Daniel, Gragg, Kaufman & Stewart 1976): after one
 // projection w' = w - V (V^H w), a second projection runs only when
-// |w'| < |w| / sqrt(2), i.e. when cancellation may have cost orthogonality.
+// |w'| < eta |w| (eta = 1/sqrt(2) by default), i.e. when cancellation may have
+// cost orthogonality: one projection leaves w' orthogonal to V to about
+// u |w| / |w'| <= u / eta (u the unit roundoff).
 // With no reorthogonalisation the step reads the basis twice (one dot pass,
 // one update pass) instead of the four reads of CGS applied twice.
 //
@@ -39,7 +41,6 @@ namespace {
 constexpr int AT = 256;       // threads per block
 constexpr int NW = AT / 32;
 constexpr int TARGET = 4 * 152;  // blocks that fill the GPU
-constexpr double REORTH2 = 0.5;  // reorthogonalise when |w'|^2 < REORTH2 |w|^2
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(AT) arn_update(ArnDev K, int j, int rows)
     if (threadIdx.x != 0) return;
     if (!SECOND) {
         const double rho = K.h1[(size_t)r * (K.m + 2) + j + 1].x;  // |w|^2 before the projection
-        const bool again = !(nw2 >= REORTH2 * rho);
+        const bool again = !(nw2 >= K.eta2 * rho);
         K.scal[8 * r + 3] = again ? 1.0 : 0.0;
         if (again) return;
     }
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(AT) arn_update_df(ArnDev K, int j, int rows)
     if (threadIdx.x != 0) return;
     if (!SECOND) {
         const double rho = K.h1[(size_t)r * (K.m + 2) + j + 1].x;
-        const bool again = !(nw2 >= REORTH2 * rho);
+        const bool again = !(nw2 >= K.eta2 * rho);
         K.scal[8 * r + 3] = again ? 1.0 : 0.0;
         if (again) return;
     }
@@ -629,6 +630,14 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
     w->bad.assign(R, 0);
     w->reorth.assign(R, 0);
     *slot = w;
+    return H2_OK;
+}
+
+h2_status arn_set_eta(ArnWork *w, double eta)
+{
+    if (!(eta >= 0.0 && eta <= 1.0)) return (set_error("GMRES: reorthogonalisation threshold must lie in [0, 1]"), H2_ERR_ARG);
+    const double e = eta == 0.0 ? std::sqrt(0.5) : eta;
+    w->K.eta2 = e * e;
     return H2_OK;
 }
 

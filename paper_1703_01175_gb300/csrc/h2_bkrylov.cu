@@ -57,6 +57,7 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
     h2_status s = arn_get(&w, h->n, m, nrhs, 0, opts->arnoldi);
     h->bkrylov = w;
     if (s != H2_OK) return s;
+    if ((s = arn_set_eta(w, opts->reorth_eta)) != H2_OK) return s;
     const int n = h->n, R = nrhs;
     const double2 *b = reinterpret_cast<const double2 *>(b_);
     double2 *x = reinterpret_cast<double2 *>(x_);

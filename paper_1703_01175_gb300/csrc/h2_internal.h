@@ -99,6 +99,7 @@ struct ArnDev {
     double2 *h1, *h2;  // [R][m+2] projection coefficients (h1[j+1] = |w|^2); h2 follows h1
     double *scal;      // [R][8]: beta, -, -, reorthogonalised flag
     int *kact;         // [R] basis columns used by the update of x
+    double eta2;       // second projection when |w'|^2 < eta2 |w|^2
     int n, m, R, np;
 };
 
@@ -123,6 +124,8 @@ struct ArnWork {
 };
 
 h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode);
+// reorthogonalisation threshold eta (0: the default 1/sqrt(2)); returns H2_ERR_ARG outside [0, 1]
+h2_status arn_set_eta(ArnWork *w, double eta);
 void arn_free(ArnWork *w);
 // rr = b - y (y NULL: rr = b); scal[8 r] = |rr_r|
 h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st);

@@ -63,6 +63,7 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
     h2_status s = arn_get(&w, h->n, m, 1, flexible ? m : 0, opts->arnoldi);
     h->krylov = w;
     if (s != H2_OK) return s;
+    if ((s = arn_set_eta(w, opts->reorth_eta)) != H2_OK) return s;
     const int n = h->n;
     h2_status worst = H2_OK;
     for (int32_t c = 0; c < nrhs; ++c) {

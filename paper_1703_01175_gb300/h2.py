@@ -56,7 +56,7 @@ ARNOLDI = {"fp64": 0, "df": 1}
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("x0_given", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("arnoldi", ctypes.c_int32)]
+                ("arnoldi", ctypes.c_int32), ("reorth_eta", ctypes.c_double)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -308,7 +308,7 @@ class H2Matrix:
         return y
 
     def gmres_batched(self, B, X=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
-                      prec="splitbf16", arnoldi="fp64", stream=None, check=True):
+                      prec="splitbf16", arnoldi="fp64", reorth_eta=0.0, stream=None, check=True):
         """Batched GMRES for B (n, nrhs) column-major complex128 on the device."""
         import torch
         if B.dtype != torch.complex128 or not B.is_cuda:
@@ -317,7 +317,7 @@ class H2Matrix:
         if X is None:
             X = torch.zeros_like(B)
         opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), 0,
-                          ARNOLDI[arnoldi])
+                          ARNOLDI[arnoldi], float(reorth_eta))
         infos = (_SolveInfo * nrhs)()
         st = torch.cuda.current_stream(B.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres_batched(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), nrhs,
@@ -340,7 +340,7 @@ class H2Matrix:
         return lib().h2_device_status(self._h)
 
     def gmres(self, b, x=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
-              precond=0, arnoldi="fp64", stream=None, check=True):
+              precond=0, arnoldi="fp64", reorth_eta=0.0, stream=None, check=True):
         """Solve A x = b on the device. b: CUDA complex128 (n,) or (n, nrhs)
         column-major. Returns (x, [info dict per RHS])."""
         import torch
@@ -350,7 +350,7 @@ class H2Matrix:
         if x is None:
             x = torch.zeros_like(b)
         opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), int(precond),
-                          ARNOLDI[arnoldi])
+                          ARNOLDI[arnoldi], float(reorth_eta))
         infos = (_SolveInfo * nrhs)()
         st = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ld,

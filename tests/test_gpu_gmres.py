@@ -121,3 +121,24 @@ def test_batched_gmres_matches_oracle(mats, prec, arnoldi):
     x1, i1 = mats["cube12"].gmres(torch.from_numpy(np.ascontiguousarray(B[:, 0])).cuda(), tol=1e-4, restart=30,
                                   refine=True)
     assert abs(info[0]["iterations"] - i1[0]["iterations"]) <= 10
+
+
+def test_reorthogonalisation_threshold(mats):
+    """eta = 1 reprojects at every step (CGS2), eta = 0.1 only under heavy
+    cancellation; both converge like the default, and eta outside [0, 1] is
+    rejected."""
+    c = cases.get("cube12")
+    b = synth.random_complex(c.n, 31)
+    bt = torch.from_numpy(b).cuda()
+    its = {}
+    for eta in (0.0, 1.0, 0.1):
+        x, info = mats["cube12"].gmres(bt, tol=1e-6, restart=30, maxit=2000, refine=True, reorth_eta=eta)
+        assert info[0]["status"] == 0
+        assert _oracle_res(c, x.cpu().numpy(), b) <= 1e-6 + 2e-7
+        its[eta] = info[0]
+    assert its[1.0]["reorth_steps"] == its[1.0]["iterations"]
+    assert its[0.1]["reorth_steps"] <= its[0.0]["reorth_steps"]
+    assert abs(its[0.1]["iterations"] - its[0.0]["iterations"]) <= 2
+    from paper_1703_01175_gb300 import h2 as h2py
+    with pytest.raises(h2py.H2Error):
+        mats["cube12"].gmres(bt, tol=1e-6, restart=30, reorth_eta=1.5)

@@ -14,10 +14,12 @@
 // up to 16 (<= 256), K staged 64 bf16 (32 complex columns) at a time in
 // 128-byte-swizzled K-major shared memory. The matrix operand is pre-packed
 // once on the device into that exact shared-memory image and fetched with one
-// bulk asynchronous copy per stage; the right-hand-side operand is gathered
-// with 16-byte cp.async from bf16 planes in which every segment starts on a
-// multiple of 4 complex entries. Two stages alternate: while the tensor core
-// works on one, the CTA fills the other.
+// bulk asynchronous copy per stage. The right-hand-side operand lives in bf16
+// planes stored chunk-major: a chunk is 4 complex entries (16 bytes) of all
+// 128 right-hand sides of a tile, 2 KB contiguous, and every input segment
+// starts on a chunk boundary, so a stage's operand is 8 bulk copies per plane
+// into the canonical no-swizzle K-major layout (8-row core matrices 128 B
+// apart, chunks 2 KB apart).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -87,18 +89,6 @@ __device__ __forceinline__ void cp16(void *dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
-// 16-byte cp.async that reads src_bytes (0 or 16) and zero-fills the rest
-__device__ __forceinline__ void cp16z(void *dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 {
@@ -110,6 +100,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     d |= (uint64_t)2 << 61;                           // 128-byte swizzle
     return d;
 }
+
+// shared-memory matrix descriptor: K-major, no swizzle, 128 rows of 16-byte
+// chunks: 8-row core matrices 128 B apart (stride), chunks 2 KB apart (leading)
+__device__ __forceinline__ uint64_t xdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)(2048 >> 4) << 16;                 // leading byte offset: next chunk along K
+    d |= (uint64_t)(128 >> 4) << 32;                  // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
+    return d;                                         // layout type 0: no swizzle
+}
+
+// byte offset of chunk c (4 complex entries) of right-hand-side tile t in a
+// chunk-major plane with nchp chunks per tile (the last one all zero)
+__device__ __forceinline__ int64_t plane_chunk(int t, int64_t nchp, int c) { return ((int64_t)t * nchp + c) * (MT * 16); }
 
 // instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n
 __device__ __forceinline__ uint32_t idesc_bf16(int n)
@@ -139,7 +145,7 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 __global__ void __launch_bounds__(UT, 1)
 umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
                  const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
-                 const __nv_bfloat16 *__restrict__ xlo, int64_t ldp, int nrhs, float2 *__restrict__ out,
+                 const __nv_bfloat16 *__restrict__ xlo, int64_t nchp, int nrhs, float2 *__restrict__ out,
                  int64_t ldo, int beta_one, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -199,8 +205,8 @@ umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ ch
             const int32_t ci = ch[q];
             const int rr = r0 + r;
             if (ci >= 0 && rr < nrhs) {
-                const __nv_bfloat16 *src = (plane ? xlo : xhi) + (int64_t)rr * ldp + 2 * (int64_t)ci;
-                cp16(dst, src);
+                const uint8_t *pl = reinterpret_cast<const uint8_t *>(plane ? xlo : xhi);
+                cp16(dst, pl + plane_chunk(blockIdx.y, nchp, ci >> 2) + r * 16);
             } else {
                 *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
             }
@@ -274,23 +280,22 @@ umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ ch
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
-// Warp-specialised, NS-stage pipelined version of umma_task_kernel.
-// Warps 0-2 produce: for each K stage they wait until its buffer is free
-// (tcgen05.commit of the MMAs that read it), issue the bulk copy of the matrix
-// image (thread 0, with expect_tx) and gather the right-hand-side chunks with
-// cp.async (zero-filled where there is no source), wait for their own copies,
-// fence them to the async proxy and arrive on the stage's `full` barrier
-// (96 arrivals + the expect_tx arrival). Warp 3 (one lane) issues the MMAs of a
-// stage once it is full and commits them to the stage's `empty` barrier. All
-// four warps then read the accumulator out of tensor memory.
+// Warp-specialised, NS-stage pipelined version of umma_task_kernel. Thread 0
+// produces: for each K stage it waits until the buffer is free (tcgen05.commit
+// of the MMAs that read it) and issues the bulk copies of the matrix image and
+// of the 16 right-hand-side chunks, which complete on the stage's `full`
+// barrier (expect_tx); a missing chunk reads the plane's zero chunk. Lane 0 of
+// warp 3 issues the MMAs of a stage once it is full and commits them to the
+// stage's `empty` barrier. All four warps then read the accumulator out of
+// tensor memory. The right-hand-side operand uses the no-swizzle layout of
+// whole 2 KB chunks; the matrix image the 128-byte-swizzled one.
 template <int NS>
 __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
                const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
-               const __nv_bfloat16 *__restrict__ xlo, int64_t ldp, int nrhs, float2 *__restrict__ out,
+               const __nv_bfloat16 *__restrict__ xlo, int64_t nchp, int nrhs, float2 *__restrict__ out,
                int64_t ldo, int beta_one, int nmax, int *__restrict__ err)
 {
-    constexpr int NPROD = 96;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const UTask tk = tasks[blockIdx.x];
@@ -310,7 +315,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     if (tid == 0) {
         abort_flag = 0;
         for (int i = 0; i < NS; ++i) {
-            mbar_init(&full[i], NPROD + 1);
+            mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -325,39 +330,36 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 3) {
-        const int pt = tid;  // 0..95
+    if (tid == 0) {
+        // producer: per stage one bulk copy of the matrix image and 16 bulk
+        // copies of right-hand-side chunks (8 per plane), all completing on
+        // the stage's `full` barrier; chunk indices are read a stage ahead
+        const uint8_t *ph = reinterpret_cast<const uint8_t *>(xhi), *pl = reinterpret_cast<const uint8_t *>(xlo);
+        const int4 *cq = reinterpret_cast<const int4 *>(chunks + tk.chunk_off);
+        int4 c0 = tk.nst > 0 ? cq[0] : make_int4(-1, -1, -1, -1), c1 = tk.nst > 0 ? cq[1] : c0;
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
+            const int ci[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            if (s + 1 < tk.nst) {
+                c0 = cq[2 * (s + 1)];
+                c1 = cq[2 * (s + 1) + 1];
+            }
             if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1)) {
                 abort_flag = 1;
                 break;
             }
             uint8_t *sx = sxb + b * 2 * XPLANE;
             uint8_t *sa = sab + b * astride;
-            if (pt == 0) {
-                mbar_expect_tx(&full[b], 2 * abytes);
-                bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
+            mbar_expect_tx(&full[b], 2 * abytes + 2 * XPLANE);
+            bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t off = plane_chunk(blockIdx.y, nchp, ci[q] >= 0 ? ci[q] >> 2 : (int)nchp - 1);
+                bulk_g2s(sx + q * 2048, ph + off, 2048, &full[b]);
+                bulk_g2s(sx + XPLANE + q * 2048, pl + off, 2048, &full[b]);
             }
-            const int32_t *ch = chunks + tk.chunk_off + (int64_t)s * (CPS / 4);
-            for (int e = pt; e < 2 * MT * 8; e += NPROD) {
-                const int plane = e >= MT * 8;
-                const int ee = e - plane * MT * 8;
-                const int r = ee >> 3, q = ee & 7;
-                uint8_t *dst = sx + plane * XPLANE + r * 128 + ((q ^ (r & 7)) << 4);
-                const int32_t ci = ch[q];
-                const int rr = r0 + r;
-                const __nv_bfloat16 *pl = plane ? xlo : xhi;
-                const bool ok = ci >= 0 && rr < nrhs;
-                const __nv_bfloat16 *src = ok ? pl + (int64_t)rr * ldp + 2 * (int64_t)ci : pl;
-                cp16z(dst, src, ok ? 16u : 0u);
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&full[b]);
         }
-    } else if (lane == 0) {
+    } else if (warp == 3 && lane == 0) {
         const uint32_t idesc = idesc_bf16(N);
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
@@ -370,11 +372,11 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
 #pragma unroll
             for (int k = 0; k < KST / 16; ++k) {
-                const uint32_t off = k * 32;
+                const uint32_t xo = k * 2 * 2048, off = k * 32;   // two chunks per K step
                 const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
-                umma(tmem, sdesc(xa + off), sdesc(aa + off), idesc, first);   // hi . hi
-                umma(tmem, sdesc(xa + off), sdesc(ab + off), idesc, 1u);      // hi . lo
-                umma(tmem, sdesc(xb + off), sdesc(aa + off), idesc, 1u);      // lo . hi
+                umma(tmem, xdesc(xa + xo), sdesc(aa + off), idesc, first);   // hi . hi
+                umma(tmem, xdesc(xa + xo), sdesc(ab + off), idesc, 1u);      // hi . lo
+                umma(tmem, xdesc(xb + xo), sdesc(aa + off), idesc, 1u);      // lo . hi
             }
             umma_commit(&empty[b]);
         }
@@ -455,17 +457,21 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
     }
 }
 
-// Scatter complex values into bf16 hi/lo planes: plane[r][2 pos(i) + {0,1}].
-// src element (r, i) at src[r * lds + map_src(i)], destination complex index map_dst(i).
+// Scatter complex values into chunk-major bf16 hi/lo planes: complex entry i
+// of right-hand side r goes to chunk i / 4 of tile r / 128, row r % 128, bytes
+// 4 (i % 4) .. + 4 (Re, Im). src element (r, i) is src[r * lds + sidx[i]] and
+// its plane index didx[i]; nchp chunks per tile.
 __global__ void split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ sidx,
                                      const int32_t *__restrict__ didx, int count, int nrhs,
-                                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t ldp)
+                                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
 {
     const int r = blockIdx.y;
     if (r >= nrhs) return;
+    const int64_t row = ((int64_t)(r / MT) * nchp) * MT + (r % MT);  // chunk 0 of the tile, row r % 128
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const float2 v = src[(int64_t)r * lds + sidx[i]];
-        const int64_t d = (int64_t)r * ldp + 2 * (int64_t)didx[i];
+        const int di = didx[i];
+        const int64_t d = (row + (int64_t)(di >> 2) * MT) * 8 + 2 * (di & 3);
         const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
         phi[d] = hx;
         phi[d + 1] = hy;
@@ -675,14 +681,16 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
     cudaFree(S->clo);
     S->xhi = S->xlo = S->chi = S->clo = nullptr;
     S->rcap = 0;
-    const size_t bx = (size_t)rpad * 2 * S->np_x * sizeof(__nv_bfloat16);
-    const size_t bc = (size_t)rpad * 2 * S->np_c * sizeof(__nv_bfloat16);
+    // chunk-major planes: per tile of 128 right-hand sides, np / 4 chunks of
+    // 2 KB plus one zero chunk (np is a multiple of 4)
+    const size_t bx = (size_t)rpad * (S->np_x / 4 + 1) * 16;
+    const size_t bc = (size_t)rpad * (S->np_c / 4 + 1) * 16;
     if (cudaMalloc(&S->xhi, bx) != cudaSuccess || cudaMalloc(&S->xlo, bx) != cudaSuccess ||
         cudaMalloc(&S->chi, bc) != cudaSuccess || cudaMalloc(&S->clo, bc) != cudaSuccess) {
         set_error("split-bf16 plane allocation failed");
         return H2_ERR_ALLOC;
     }
-    // padding entries stay zero: the scatter kernels never write them
+    // padding entries and the zero chunks stay zero: the scatter kernels never write them
     UM_CUDA(cudaMemset(S->xhi, 0, bx));
     UM_CUDA(cudaMemset(S->xlo, 0, bx));
     UM_CUDA(cudaMemset(S->chi, 0, bc));
@@ -692,7 +700,7 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
 }
 
 static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_bfloat16 *phi,
-                               const __nv_bfloat16 *plo, int64_t ldp, int nrhs, float2 *out, int64_t ldo,
+                               const __nv_bfloat16 *plo, int64_t nchp, int nrhs, float2 *out, int64_t ldo,
                                int beta, cudaStream_t st)
 {
     if (U.ntile == 0) return cudaSuccess;
@@ -700,14 +708,14 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_
     if (S->pipeline) {
         if (umma_ws_smem_bytes(3, U.nmax) <= S->dyn_smem_limit) {
             umma_ws_kernel<3><<<grid, UT, umma_ws_smem_bytes(3, U.nmax), st>>>(
-                U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs, out, ldo, beta, U.nmax, S->d_err);
+                U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, beta, U.nmax, S->d_err);
         } else {
             umma_ws_kernel<2><<<grid, UT, umma_ws_smem_bytes(2, U.nmax), st>>>(
-                U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs, out, ldo, beta, U.nmax, S->d_err);
+                U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, beta, U.nmax, S->d_err);
         }
         return cudaGetLastError();
     }
-    umma_task_kernel<<<grid, UT, umma_smem_bytes(), st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, ldp, nrhs,
+    umma_task_kernel<<<grid, UT, umma_smem_bytes(), st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs,
                                                           out, ldo, beta, S->d_err);
     return cudaGetLastError();
 }
@@ -749,26 +757,26 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     const int64_t ldc = std::max<int64_t>(2, 2 * h->ktot);
     float2 *coef = reinterpret_cast<float2 *>(h->d_coefm);
     const float2 *mat = h->d_mat;
-    const int64_t ldpx = 2 * S->np_x, ldpc = 2 * S->np_c;
+    const int64_t nchx = S->np_x / 4 + 1, nchc = S->np_c / 4 + 1;  // chunks per tile, zero chunk last
     UM_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * ldc * nrhs, st));
     {
         dim3 g(std::min(64, (S->nx + 255) / 256), nrhs);
-        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xsrc, S->d_xdst, S->nx, nrhs, bf(S->xhi), bf(S->xlo), ldpx);
+        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xsrc, S->d_xdst, S->nx, nrhs, bf(S->xhi), bf(S->xlo), nchx);
         UM_CUDA(cudaGetLastError());
     }
     UM_CUDA(cudaEventRecord(h->ev_fork, st));
     UM_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
-    UM_CUDA(launch_umma(S->near, S, bf(S->xhi), bf(S->xlo), ldpx, nrhs, y, ldy, 0, h->s_aux));
+    UM_CUDA(launch_umma(S->near, S, bf(S->xhi), bf(S->xlo), nchx, nrhs, y, ldy, 0, h->s_aux));
     UM_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
     UM_CUDA(launch_phase_mrhs_f32(h->upleaf, mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
     for (int l = h->nlev - 1; l >= 0; --l)
         UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
     {
         dim3 g(std::min(64, (S->nc + 255) / 256), nrhs);
-        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_csrc, S->d_cdst, S->nc, nrhs, bf(S->chi), bf(S->clo), ldpc);
+        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_csrc, S->d_cdst, S->nc, nrhs, bf(S->chi), bf(S->clo), nchc);
         UM_CUDA(cudaGetLastError());
     }
-    UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), ldpc, nrhs, coef, ldc, 0, st));
+    UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), nchc, nrhs, coef, ldc, 0, st));
     for (int l = 0; l < h->nlev; ++l)
         UM_CUDA(launch_phase_mrhs_f32(h->down[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 1, st));
     UM_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));

@@ -79,12 +79,11 @@ struct UPhase {
 struct SplitState {
     UPhase near, couple;
     int64_t np_x = 0, np_c = 0;   // padded complex lengths of the x and coefficient planes
-    int nx = 0, nc = 0;           // scattered entries
-    int32_t *d_xsrc = nullptr, *d_xdst = nullptr, *d_csrc = nullptr, *d_cdst = nullptr;
+    int32_t *d_xpos = nullptr, *d_cpos = nullptr;  // plane position -> source index (-1: padding)
     void *xhi = nullptr, *xlo = nullptr, *chi = nullptr, *clo = nullptr;  // bf16 planes
     int rcap = 0;
     int *d_err = nullptr;         // set when a bounded wait ran out
-    bool pipeline = true;         // warp-specialised multi-stage kernel (else the two-stage one)
+    bool pipeline = true;         // deepest pipeline that fits (else two stages)
     size_t dyn_smem_limit = 0;    // dynamic shared memory a block may use
 };
 
@@ -186,7 +185,7 @@ struct h2_handle {
     std::vector<GraphEntry> graphs;
     uint64_t graph_clock = 0;
     bool use_graphs = true;
-    bool tc_pipeline = true;          // split-bf16: warp-specialised multi-stage tensor-core kernel
+    bool tc_pipeline = true;          // split-bf16: deepest tensor-core pipeline that fits (else two stages)
     cudaStream_t s_cap = nullptr;
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
 };

@@ -35,10 +35,11 @@ namespace h2 {
 namespace {
 
 constexpr int UT = 128;               // threads per CTA (4 warps)
-constexpr int KST = 64;               // bf16 K elements per stage (128 bytes per row)
+constexpr int KST = 32;               // bf16 K elements per stage
 constexpr int CPS = KST / 2;          // complex columns per stage
+constexpr int NCH = KST / 8;          // 16-byte K chunks per stage
 constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
-constexpr int XPLANE = MT * 128;      // bytes of one X plane image per stage
+constexpr int XPLANE = NCH * MT * 16; // bytes of one X plane image per stage
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -84,21 +85,16 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-__device__ __forceinline__ void cp16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+// shared-memory matrix descriptor of the matrix operand: K-major, no swizzle,
+// N rows of 16-byte chunks: 8-row core matrices 128 B apart, chunks 16 N B apart
+__device__ __forceinline__ uint64_t bdesc(uint32_t saddr, int n)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
-    d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)((16 * n) >> 4) << 16;             // leading byte offset: next chunk along K
+    d |= (uint64_t)(128 >> 4) << 32;                  // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
-    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
-    return d;
+    return d;                                         // layout type 0: no swizzle
 }
 
 // shared-memory matrix descriptor: K-major, no swizzle, 128 rows of 16-byte
@@ -141,154 +137,15 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 
 }  // namespace
 
-// One tile of a split-bf16 task (see h2_internal.h: UTask).
-__global__ void __launch_bounds__(UT, 1)
-umma_task_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
-                 const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
-                 const __nv_bfloat16 *__restrict__ xlo, int64_t nchp, int nrhs, float2 *__restrict__ out,
-                 int64_t ldo, int beta_one, int *__restrict__ err)
-{
-    extern __shared__ __align__(1024) uint8_t smem_raw[];
-    // 1024-byte aligned carve-up: [X0 hi|lo][X1 hi|lo][A0 hi|lo][A1 hi|lo], barriers at the end
-    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const UTask tk = tasks[blockIdx.x];
-    const int N = tk.n;
-    const uint32_t abytes = (uint32_t)N * 128u;  // one plane of the matrix image per stage
-    uint8_t *sx[2] = {base, base + 2 * XPLANE};
-    uint8_t *sa[2] = {base + 4 * XPLANE, base + 4 * XPLANE + 2 * 256 * 128};
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + 4 * XPLANE + 4 * 256 * 128);
-    uint64_t *full = bars;       // [2] matrix image arrived
-    uint64_t *done = bars + 2;   // [2] MMAs of that stage finished
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 4);
-    __shared__ int abort_flag;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int r0 = blockIdx.y * MT;
-    if (tid == 0) {
-        abort_flag = 0;
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&done[i], 1);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = idesc_bf16(N);
-
-    for (int s = 0; s < tk.nst; ++s) {
-        const int b = s & 1;
-        if (s >= 2) {
-            if (!mbar_wait(&done[b], ((s - 2) >> 1) & 1)) abort_flag = 1;
-        }
-        __syncthreads();
-        if (abort_flag) break;
-        if (tid == 0) {
-            const uint8_t *img = images + tk.img_off + (int64_t)s * 2 * abytes;
-            mbar_expect_tx(&full[b], 2 * abytes);
-            bulk_g2s(sa[b], img, 2 * abytes, &full[b]);
-        }
-        // gather the right-hand-side tile: 128 rows x 8 chunks of 16 B, two planes
-        const int32_t *ch = chunks + tk.chunk_off + (int64_t)s * (CPS / 4);
-        for (int e = tid; e < 2 * MT * 8; e += UT) {
-            const int plane = e >= MT * 8;
-            const int ee = e - plane * MT * 8;
-            const int r = ee >> 3, q = ee & 7;
-            uint8_t *dst = sx[b] + plane * XPLANE + r * 128 + ((q ^ (r & 7)) << 4);
-            const int32_t ci = ch[q];
-            const int rr = r0 + r;
-            if (ci >= 0 && rr < nrhs) {
-                const uint8_t *pl = reinterpret_cast<const uint8_t *>(plane ? xlo : xhi);
-                cp16(dst, pl + plane_chunk(blockIdx.y, nchp, ci >> 2) + r * 16);
-            } else {
-                *reinterpret_cast<uint4 *>(dst) = make_uint4(0, 0, 0, 0);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            if (!mbar_wait(&full[b], (s >> 1) & 1)) {
-                abort_flag = 1;
-            } else {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t xa = smem_u32(sx[b]), xb = xa + XPLANE;
-                const uint32_t aa = smem_u32(sa[b]), ab = aa + abytes;
-#pragma unroll
-                for (int k = 0; k < KST / 16; ++k) {
-                    const uint32_t off = k * 32;
-                    const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
-                    umma(tmem, sdesc(xa + off), sdesc(aa + off), idesc, first);   // hi . hi
-                    umma(tmem, sdesc(xa + off), sdesc(ab + off), idesc, 1u);      // hi . lo
-                    umma(tmem, sdesc(xb + off), sdesc(aa + off), idesc, 1u);      // lo . hi
-                }
-                umma_commit(&done[b]);
-            }
-        }
-    }
-    __syncthreads();
-    const bool ok = !abort_flag && tk.nst > 0;
-    if (ok) {
-        const int last = tk.nst - 1;
-        if (!mbar_wait(&done[last & 1], (last >> 1) & 1)) abort_flag = 1;
-    }
-    __syncthreads();
-    if (abort_flag && tid == 0) atomicExch(err, 1);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_flag && tk.nst > 0) {
-        // epilogue: lane r of TMEM holds D[r][0..N) = (Re, Im) pairs of output rows
-        const int r = r0 + warp * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int j0 = 0; j0 < N; j0 += 16) {
-            uint32_t v[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(tl + (uint32_t)j0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (r < nrhs) {
-                float2 *o = out + (int64_t)r * ldo + tk.out_off;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int i = j0 / 2 + q;
-                    if (i < tk.m) {
-                        float2 val = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
-                        if (beta_one) {
-                            const float2 p = o[i];
-                            val.x += p.x;
-                            val.y += p.y;
-                        }
-                        o[i] = val;
-                    }
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
-}
-
-// Warp-specialised, NS-stage pipelined version of umma_task_kernel. Thread 0
+// One tile of a split-bf16 task (see h2_internal.h: UTask), NS-stage pipelined. Thread 0
 // produces: for each K stage it waits until the buffer is free (tcgen05.commit
 // of the MMAs that read it) and issues the bulk copies of the matrix image and
 // of the 16 right-hand-side chunks, which complete on the stage's `full`
 // barrier (expect_tx); a missing chunk reads the plane's zero chunk. Lane 0 of
 // warp 3 issues the MMAs of a stage once it is full and commits them to the
 // stage's `empty` barrier. All four warps then read the accumulator out of
-// tensor memory. The right-hand-side operand uses the no-swizzle layout of
-// whole 2 KB chunks; the matrix image the 128-byte-swizzled one.
+// tensor memory. Both operands use the no-swizzle K-major layout: right-hand
+// sides as whole 2 KB chunks, the matrix image as NCH chunks of N rows.
 template <int NS>
 __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
@@ -300,8 +157,8 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const UTask tk = tasks[blockIdx.x];
     const int N = tk.n;
-    const uint32_t abytes = (uint32_t)N * 128u;
-    const uint32_t astride = 2u * (uint32_t)nmax * 128u;
+    const uint32_t abytes = (uint32_t)N * 16u * NCH;       // one plane of the matrix image per stage
+    const uint32_t astride = 2u * (uint32_t)nmax * 16u * NCH;
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
     uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
@@ -331,19 +188,17 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        // producer: per stage one bulk copy of the matrix image and 16 bulk
-        // copies of right-hand-side chunks (8 per plane), all completing on
+        // producer: per stage one bulk copy of the matrix image and 2 NCH bulk
+        // copies of right-hand-side chunks (NCH per plane), all completing on
         // the stage's `full` barrier; chunk indices are read a stage ahead
         const uint8_t *ph = reinterpret_cast<const uint8_t *>(xhi), *pl = reinterpret_cast<const uint8_t *>(xlo);
+        static_assert(NCH == 4, "one int4 of chunk indices per stage");
         const int4 *cq = reinterpret_cast<const int4 *>(chunks + tk.chunk_off);
-        int4 c0 = tk.nst > 0 ? cq[0] : make_int4(-1, -1, -1, -1), c1 = tk.nst > 0 ? cq[1] : c0;
+        int4 c0 = tk.nst > 0 ? cq[0] : make_int4(-1, -1, -1, -1);
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
-            const int ci[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-            if (s + 1 < tk.nst) {
-                c0 = cq[2 * (s + 1)];
-                c1 = cq[2 * (s + 1) + 1];
-            }
+            const int ci[NCH] = {c0.x, c0.y, c0.z, c0.w};
+            if (s + 1 < tk.nst) c0 = cq[s + 1];
             if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1)) {
                 abort_flag = 1;
                 break;
@@ -353,7 +208,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             mbar_expect_tx(&full[b], 2 * abytes + 2 * XPLANE);
             bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < NCH; ++q) {
                 const int64_t off = plane_chunk(blockIdx.y, nchp, ci[q] >= 0 ? ci[q] >> 2 : (int)nchp - 1);
                 bulk_g2s(sx + q * 2048, ph + off, 2048, &full[b]);
                 bulk_g2s(sx + XPLANE + q * 2048, pl + off, 2048, &full[b]);
@@ -372,11 +227,11 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
 #pragma unroll
             for (int k = 0; k < KST / 16; ++k) {
-                const uint32_t xo = k * 2 * 2048, off = k * 32;   // two chunks per K step
+                const uint32_t xo = k * 2 * 2048, bo = k * 2 * 16 * (uint32_t)N;   // two chunks per K step
                 const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
-                umma(tmem, xdesc(xa + xo), sdesc(aa + off), idesc, first);   // hi . hi
-                umma(tmem, xdesc(xa + xo), sdesc(ab + off), idesc, 1u);      // hi . lo
-                umma(tmem, xdesc(xb + xo), sdesc(aa + off), idesc, 1u);      // lo . hi
+                umma(tmem, xdesc(xa + xo), bdesc(aa + bo, N), idesc, first);   // hi . hi
+                umma(tmem, xdesc(xa + xo), bdesc(ab + bo, N), idesc, 1u);      // hi . lo
+                umma(tmem, xdesc(xb + xo), bdesc(aa + bo, N), idesc, 1u);      // lo . hi
             }
             umma_commit(&empty[b]);
         }
@@ -425,7 +280,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
-size_t umma_ws_smem_bytes(int ns, int nmax) { return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 128) + 1024 + 128; }
+size_t umma_ws_smem_bytes(int ns, int nmax) { return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * NCH) + 1024 + 128; }
 
 // Pack the real-expanded, bf16-split matrix images of every tile/stage.
 __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
@@ -437,7 +292,7 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
     const int N = tk.n;
     const int s = blockIdx.y;
     if (s >= tk.nst) return;
-    uint8_t *img = images + tk.img_off + (int64_t)s * 2 * N * 128;
+    uint8_t *img = images + tk.img_off + (int64_t)s * 2 * N * 16 * NCH;
     for (int e = threadIdx.x; e < N * KST; e += blockDim.x) {
         const int nr = e / KST, kk = e % KST;
         const int i = pi.row0 + (nr >> 1);                 // complex row in the task matrix
@@ -451,36 +306,48 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
         }
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const int byte = nr * 128 + ((((kk * 2) >> 4) ^ (nr & 7)) << 4) + ((kk * 2) & 15);
+        const int byte = (kk >> 3) * (16 * N) + nr * 16 + (kk & 7) * 2;   // chunk, row, element
         *reinterpret_cast<__nv_bfloat16 *>(img + byte) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(img + N * 128 + byte) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(img + N * 16 * NCH + byte) = lo;
     }
 }
 
-// Scatter complex values into chunk-major bf16 hi/lo planes: complex entry i
-// of right-hand side r goes to chunk i / 4 of tile r / 128, row r % 128, bytes
-// 4 (i % 4) .. + 4 (Re, Im). src element (r, i) is src[r * lds + sidx[i]] and
-// its plane index didx[i]; nchp chunks per tile.
-__global__ void split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ sidx,
-                                     const int32_t *__restrict__ didx, int count, int nrhs,
-                                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
+// Fill chunk-major bf16 hi/lo planes: plane position d of right-hand side r
+// holds src[r * lds + pos[d]] (zero where pos[d] < 0), stored in chunk d / 4
+// of tile r / 128, row r % 128, bytes 4 (d % 4) .. + 4 (Re, Im); nchp chunks
+// per tile. A block transposes 32 positions x 32 right-hand sides through
+// shared memory, so that reads run along positions and each warp writes 32
+// consecutive 16-byte chunk rows.
+__global__ void __launch_bounds__(256)
+split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ pos, int np, int nrhs,
+                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
 {
-    const int r = blockIdx.y;
-    if (r >= nrhs) return;
-    const int64_t row = ((int64_t)(r / MT) * nchp) * MT + (r % MT);  // chunk 0 of the tile, row r % 128
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        const float2 v = src[(int64_t)r * lds + sidx[i]];
-        const int di = didx[i];
-        const int64_t d = (row + (int64_t)(di >> 2) * MT) * 8 + 2 * (di & 3);
-        const __nv_bfloat16 hx = __float2bfloat16_rn(v.x), hy = __float2bfloat16_rn(v.y);
-        phi[d] = hx;
-        phi[d + 1] = hy;
-        plo[d] = __float2bfloat16_rn(v.x - __bfloat162float(hx));
-        plo[d + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hy));
+    __shared__ float2 tile[32][33];
+    const int d0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int pd = d0 + tx < np ? pos[d0 + tx] : -1;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = r0 + rr;
+        tile[rr][tx] = (pd >= 0 && r < nrhs) ? src[(int64_t)r * lds + pd] : make_float2(0.f, 0.f);
     }
+    __syncthreads();
+    const int r = r0 + tx, c = (d0 >> 2) + ty;
+    if (r >= nrhs || 4 * c >= np) return;
+    __align__(16) __nv_bfloat16 hv[8];
+    __align__(16) __nv_bfloat16 lv[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 v = tile[tx][4 * ty + k];
+        hv[2 * k] = __float2bfloat16_rn(v.x);
+        hv[2 * k + 1] = __float2bfloat16_rn(v.y);
+        lv[2 * k] = __float2bfloat16_rn(v.x - __bfloat162float(hv[2 * k]));
+        lv[2 * k + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hv[2 * k + 1]));
+    }
+    const int64_t off = (((int64_t)(r / MT) * nchp + c) * MT + (r % MT)) * 8;
+    *reinterpret_cast<uint4 *>(phi + off) = *reinterpret_cast<const uint4 *>(hv);
+    *reinterpret_cast<uint4 *>(plo + off) = *reinterpret_cast<const uint4 *>(lv);
 }
 
-size_t umma_smem_bytes() { return 4 * XPLANE + 4 * 256 * 128 + 64 + 1024; }
 
 }  // namespace h2
 
@@ -532,7 +399,7 @@ static h2_status build_uphase(h2_handle *h, const Phase &ph, const std::vector<S
             u.nst = nst;
             u.img_off = img;
             u.chunk_off = chunk_off;
-            img += (int64_t)nst * 2 * u.n * 128;
+            img += (int64_t)nst * 2 * u.n * 16 * NCH;
             tiles.push_back(u);
             UPackInfo pi{};
             pi.row0 = row0;
@@ -606,16 +473,17 @@ static h2_status split_init(h2_handle *h)
         q += (h->rank[t] + 3) / 4 * 4;
     }
     S->np_c = std::max<int64_t>(8, (q + 3) / 4 * 4);
-    S->nx = (int)xs.size();
-    S->nc = (int)cs.size();
+    // plane position -> source index (-1: padding)
+    std::vector<int32_t> xpos(S->np_x, -1), cpos(S->np_c, -1);
+    for (size_t k = 0; k < xs.size(); ++k) xpos[xd[k]] = xs[k];
+    for (size_t k = 0; k < cs.size(); ++k) cpos[cd[k]] = cs[k];
     auto up = [&](const std::vector<int32_t> &v, int32_t **d) -> h2_status {
         UM_CUDA(cudaMalloc(d, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
         if (!v.empty()) UM_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         return H2_OK;
     };
     h2_status st;
-    if ((st = up(xs, &S->d_xsrc)) != H2_OK || (st = up(xd, &S->d_xdst)) != H2_OK ||
-        (st = up(cs, &S->d_csrc)) != H2_OK || (st = up(cd, &S->d_cdst)) != H2_OK) {
+    if ((st = up(xpos, &S->d_xpos)) != H2_OK || (st = up(cpos, &S->d_cpos)) != H2_OK) {
         h->split = S;
         return st;
     }
@@ -646,25 +514,23 @@ static h2_status split_init(h2_handle *h)
     h->split = S;
     if ((st = build_uphase(h, h->near, hsegs, nbase, S->near)) != H2_OK) return st;
     if ((st = build_uphase(h, h->couple, hsegs, cbase, S->couple)) != H2_OK) return st;
-    UM_CUDA(cudaFuncSetAttribute(umma_task_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)umma_smem_bytes()));
     {
         // dynamic shared memory limit = opt-in per-block maximum minus the kernels' static shared memory
         int optin = 0;
         UM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        cudaFuncAttributes fa2{}, fa3{};
-        UM_CUDA(cudaFuncGetAttributes(&fa2, umma_ws_kernel<2>));
-        UM_CUDA(cudaFuncGetAttributes(&fa3, umma_ws_kernel<3>));
-        const size_t st = std::max(fa2.sharedSizeBytes, fa3.sharedSizeBytes);
-        S->dyn_smem_limit = optin > (int)st ? (size_t)optin - st : 0;
-        if (S->pipeline && umma_ws_smem_bytes(2, std::max(S->near.nmax, S->couple.nmax)) > S->dyn_smem_limit)
-            S->pipeline = false;  // tiles too wide for two stages: keep the two-stage kernel
-        if (S->pipeline) {
-            UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S->dyn_smem_limit));
-            UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)S->dyn_smem_limit));
+        cudaFuncAttributes fa{};
+        UM_CUDA(cudaFuncGetAttributes(&fa, umma_ws_kernel<2>));
+        S->dyn_smem_limit = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        if (umma_ws_smem_bytes(2, std::max(S->near.nmax, S->couple.nmax)) > S->dyn_smem_limit) {
+            set_error("split-bf16: two pipeline stages of the widest tile exceed shared memory");
+            return H2_ERR_STATE;
         }
+        const int lim = (int)S->dyn_smem_limit;
+        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     }
     UM_CUDA(cudaMalloc(&S->d_err, sizeof(int)));
     UM_CUDA(cudaMemset(S->d_err, 0, sizeof(int)));
@@ -699,24 +565,33 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
     return H2_OK;
 }
 
+// Deepest pipeline that fits in shared memory (two stages when the pipeline
+// option is off).
 static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_bfloat16 *phi,
                                const __nv_bfloat16 *plo, int64_t nchp, int nrhs, float2 *out, int64_t ldo,
                                int beta, cudaStream_t st)
 {
     if (U.ntile == 0) return cudaSuccess;
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
-    if (S->pipeline) {
-        if (umma_ws_smem_bytes(3, U.nmax) <= S->dyn_smem_limit) {
-            umma_ws_kernel<3><<<grid, UT, umma_ws_smem_bytes(3, U.nmax), st>>>(
-                U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, beta, U.nmax, S->d_err);
-        } else {
-            umma_ws_kernel<2><<<grid, UT, umma_ws_smem_bytes(2, U.nmax), st>>>(
-                U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, beta, U.nmax, S->d_err);
-        }
-        return cudaGetLastError();
+    int ns = 2;
+    if (S->pipeline)
+        for (int c = 6; c > 2; --c)
+            if (umma_ws_smem_bytes(c, U.nmax) <= S->dyn_smem_limit) {
+                ns = c;
+                break;
+            }
+    const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
+#define H2_UMMA_LAUNCH(NSV)                                                                                   \
+    umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, \
+                                              beta, U.nmax, S->d_err)
+    switch (ns) {
+        case 6: H2_UMMA_LAUNCH(6); break;
+        case 5: H2_UMMA_LAUNCH(5); break;
+        case 4: H2_UMMA_LAUNCH(4); break;
+        case 3: H2_UMMA_LAUNCH(3); break;
+        default: H2_UMMA_LAUNCH(2); break;
     }
-    umma_task_kernel<<<grid, UT, umma_smem_bytes(), st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs,
-                                                          out, ldo, beta, S->d_err);
+#undef H2_UMMA_LAUNCH
     return cudaGetLastError();
 }
 
@@ -731,10 +606,8 @@ void h2_free_split(h2_handle *h)
         cudaFree(U->d_chunks);
         cudaFree(U->d_images);
     }
-    cudaFree(S->d_xsrc);
-    cudaFree(S->d_xdst);
-    cudaFree(S->d_csrc);
-    cudaFree(S->d_cdst);
+    cudaFree(S->d_xpos);
+    cudaFree(S->d_cpos);
     cudaFree(S->xhi);
     cudaFree(S->xlo);
     cudaFree(S->chi);
@@ -760,8 +633,8 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     const int64_t nchx = S->np_x / 4 + 1, nchc = S->np_c / 4 + 1;  // chunks per tile, zero chunk last
     UM_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * ldc * nrhs, st));
     {
-        dim3 g(std::min(64, (S->nx + 255) / 256), nrhs);
-        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xsrc, S->d_xdst, S->nx, nrhs, bf(S->xhi), bf(S->xlo), nchx);
+        dim3 g((unsigned)((S->np_x + 31) / 32), (nrhs + 31) / 32);
+        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xpos, (int)S->np_x, nrhs, bf(S->xhi), bf(S->xlo), nchx);
         UM_CUDA(cudaGetLastError());
     }
     UM_CUDA(cudaEventRecord(h->ev_fork, st));
@@ -772,8 +645,8 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     for (int l = h->nlev - 1; l >= 0; --l)
         UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
     {
-        dim3 g(std::min(64, (S->nc + 255) / 256), nrhs);
-        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_csrc, S->d_cdst, S->nc, nrhs, bf(S->chi), bf(S->clo), nchc);
+        dim3 g((unsigned)((S->np_c + 31) / 32), (nrhs + 31) / 32);
+        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_cpos, (int)S->np_c, nrhs, bf(S->chi), bf(S->clo), nchc);
         UM_CUDA(cudaGetLastError());
     }
     UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), nchc, nrhs, coef, ldc, 0, st));

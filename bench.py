@@ -489,7 +489,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", dest="learned", action="store_false",
                     help="skip the learned-preconditioner leg")
-    ap.add_argument("--gmres-batch", type=int, default=32, help="right-hand sides of the batched solve (0: skip)")
+    ap.add_argument("--gmres-batch", type=int, default=128, help="right-hand sides of the batched solve (0: skip)")
     ap.add_argument("--gmres-restart", type=int, default=400, help="restart of the batched / plain comparison")
     ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--fp-rates", action="store_true",

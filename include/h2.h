@@ -114,8 +114,8 @@ typedef struct {
  * "device=<int>" (default 0), "graphs=0|1" (default 1: the single-RHS FP32
  * product is captured into a CUDA graph per (x, y) pair on first use and
  * replayed afterwards; at most 8 graphs are kept, least recently used first
- * out), "tc_pipeline=0|1" (default 1: the split-bf16 products use the
- * warp-specialised multi-stage tensor-core kernel; 0: the two-stage one).
+ * out), "tc_pipeline=0|1" (default 1: the split-bf16 tensor-core kernel runs
+ * the deepest pipeline that fits in shared memory, up to 6 stages; 0: two).
  */
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);

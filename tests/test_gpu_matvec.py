@@ -135,9 +135,9 @@ def test_multi_rhs_fp32_matches_oracle(loaded, name, R):
 @pytest.mark.parametrize("name,R", [("cube12", 128), ("cube12", 5), ("ragged", 130), ("slab", 64),
                                     ("array", 17), ("tiny_leaves", 3)])
 def test_splitbf16_tensor_cores_match_oracle(loaded, name, R, pipeline):
-    """Split-bf16 tcgen05 path (warp-specialised multi-stage kernel and the
-    two-stage kernel): within eps = 1e-4 of the oracle's FP64 product
-    (spec bound for the lower-precision form)."""
+    """Split-bf16 tcgen05 path (deepest pipeline and two stages): within
+    eps = 1e-4 of the oracle's FP64 product
+    (the accuracy stated for the lower-precision form)."""
     from oracle import h2mv
     c = cases.get(name)
     A = _mat(loaded, name, tc_pipeline=pipeline)

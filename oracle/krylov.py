@@ -11,7 +11,9 @@ Saad 1993) stores the preconditioned directions z_j = M(v_j) and updates
 x += Z y.
 
 Pin (tests/test_oracle_krylov.py): the solution agrees with LAPACK's dense
-solve, and the Arnoldi relation A V_m = V_{m+1} H_m holds.
+solve, and the Arnoldi relation A V_m = V_{m+1} H_m holds. The paper's own
+solver, BiCGStab, is here too (`bicgstab`), pinned the same way and by its
+exact termination on operators with few distinct eigenvalues.
 """
 from __future__ import annotations
 
@@ -108,3 +110,50 @@ def arnoldi(apply_A, v0: np.ndarray, m: int):
         H[j + 1, j] = np.linalg.norm(w)
         V[:, j + 1] = w / H[j + 1, j]
     return V, H
+
+
+def bicgstab(apply_A, b: np.ndarray, tol: float, maxit: int = 1000, x0=None):
+    """BiCGStab (van der Vorst 1992), the paper's solver (Sec. V), for complex
+    systems: the shadow residual is r0, inner products (u, v) = u^H v.
+
+    Each iteration takes two products: v = A p, then t = A s. The iterate
+    stops when the recursive residual r falls below tol * ||b|| (the returned
+    history holds ||r|| / ||b|| per iteration); breakdown (rho = 0,
+    (r0, v) = 0 or (t, t) = 0) ends the solve. Returns (x, iterations, history).
+    """
+    b = np.asarray(b, dtype=np.complex128)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128) if x0 is None else np.array(x0, dtype=np.complex128)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - apply_A(x)
+    rhat = r.copy()
+    hist = [np.linalg.norm(r) / bnorm]
+    rho_old = alpha = omega = 1.0 + 0.0j
+    v = np.zeros(n, dtype=np.complex128)
+    p = np.zeros(n, dtype=np.complex128)
+    it = 0
+    while hist[-1] > tol and it < maxit:
+        rho = np.vdot(rhat, r)
+        if rho == 0:
+            break
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = apply_A(p)
+        d = np.vdot(rhat, v)
+        if d == 0:
+            break
+        alpha = rho / d
+        s = r - alpha * v
+        t = apply_A(s)
+        tt = np.vdot(t, t).real
+        omega = np.vdot(t, s) / tt if tt > 0 else 0.0
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho_old = rho
+        it += 1
+        hist.append(np.linalg.norm(r) / bnorm)
+        if omega == 0:
+            break
+    return x, it, hist

@@ -62,3 +62,38 @@ def test_h2_gmres_residual_cube8():
     assert hist[-1] <= w.tol
     # the H^2 solution solves the dense system to about the representation error
     assert np.linalg.norm(Zt @ x - b) <= 1e-4 * np.linalg.norm(b)
+
+
+def test_bicgstab_matches_dense_solve_cube8():
+    w = synth.workload("cube8")
+    v = w.voxels
+    Z = vie.assemble_Z(v.centres, v.dv, v.eps_r, K)
+    b = synth.default_rhs(w)
+    x, it, hist = krylov.bicgstab(lambda q: Z @ q, b, 1e-10, maxit=500)
+    xd = np.linalg.solve(Z, b)
+    assert hist[-1] <= 1e-10
+    assert np.linalg.norm(Z @ x - b) <= 2e-10 * np.linalg.norm(b)   # recursive and true residual agree
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_bicgstab_exact_on_two_eigenvalues():
+    """A = Q diag(l1, l2) Q^-1 has a minimal polynomial of degree 2: the
+    BiCG part terminates after two steps, so BiCGStab converges in at most 2
+    iterations (in exact arithmetic; here to rounding)."""
+    rng = np.random.default_rng(3)
+    n = 12
+    Q = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    d = np.where(np.arange(n) < 5, 2.0 + 1.0j, 0.5 - 0.25j)
+    A = Q @ np.diag(d) @ np.linalg.inv(Q)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, hist = krylov.bicgstab(lambda q: A @ q, b, 1e-9, maxit=50)
+    assert it <= 2
+    assert np.linalg.norm(A @ x - b) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_bicgstab_identity_and_zero_rhs():
+    b = synth.random_complex(10, 4)
+    x, it, hist = krylov.bicgstab(lambda q: 3.0 * q, b, 1e-12)
+    assert it == 1 and np.allclose(x, b / 3.0)
+    x, it, hist = krylov.bicgstab(lambda q: q, np.zeros(5, complex), 1e-12)
+    assert it == 0 and not np.any(x)

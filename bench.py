@@ -289,6 +289,19 @@ def run_ours(args, rank, world, local_rank):
                      "rel_res": info[0]["rel_res"], "status": info[0]["status"],
                      "reorth_steps": info[0]["reorth_steps"]}
 
+    # the paper's solver: BiCGStab, FP32 products, true residual checked with the FP64-accumulated product
+    A.bicgstab(b, tol=w.tol, maxit=10, refine=True)  # warm-up (workspace)
+    torch.cuda.synchronize(dev)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    xs, info = A.bicgstab(b, tol=w.tol, maxit=3000, refine=True)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    gm["bicgstab"] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
+                      "products": 2 * info[0]["iterations"], "restarts": info[0]["restarts"],
+                      "rel_res": info[0]["rel_res"], "status": info[0]["status"]}
+
     # multi-RHS products: R right-hand sides at once (split-bf16 tensor cores vs FP32 CUDA cores)
     mr = None
     if args.mrhs > 0:

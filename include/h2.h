@@ -288,6 +288,24 @@ h2_status h2_gmres_batched(h2_handle *h, const void *b, void *x, int32_t nrhs, i
                            const h2_solve_opts *opts, h2_prec prec, h2_solve_info *info, void *stream);
 
 /*
+ * Solve A x = b by BiCGStab (van der Vorst 1992), the paper's solver (Sec. V),
+ * around the H^2 product: FP32 products inside the iteration, FP64 vectors,
+ * inner products and scalars on the device (shadow residual r0, complex inner
+ * products u^H v). One iteration is two products. opts: tol, maxit (maximum
+ * iterations), refine (a recursive residual below tol is checked against the
+ * true residual b - A x with the accumulated product, FP64ACC, or DFACC when
+ * arnoldi = 1, and the iteration restarts from x while it is above tol),
+ * x0_given; restart and reorth_eta are not used; precond must be 0. A
+ * breakdown (rho, (r0, A p) or |A s| zero) restarts from the true residual.
+ * b, x: device c128, nrhs columns (ld >= N), solved one after another;
+ * info[c].iterations counts iterations, info[c].restarts the restarts.
+ * Returns H2_OK when every right-hand side converged, H2_ERR_NOT_CONVERGED,
+ * H2_ERR_BREAKDOWN, or an argument / CUDA error.
+ */
+h2_status h2_bicgstab(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld, const h2_solve_opts *opts,
+                      h2_solve_info *info, void *stream);
+
+/*
  * Load (or, with n_layers = 0, remove) the learned preconditioner used by
  * h2_gmres with precond = 1: a chain of 3x3x3 convolutions on the
  * Dx x Dy x Dz voxel grid (include/h2nn.h). Unknown 3 p + c of the operator is

@@ -235,6 +235,7 @@ void h2_free(h2_handle *h)
     h2_free_split(h);
     h2_free_precond(h);
     h2_free_bkrylov(h);
+    h2_free_bicgstab(h);
     cudaFree(h->d_mat);
     cudaFree(h->d_segs);
     cudaFree(h->d_tasks);

@@ -33,6 +33,7 @@
 #include <string>
 
 #include "h2_df.cuh"
+#include "h2_reduce.cuh"
 #include "h2_internal.h"
 
 namespace h2 {
@@ -45,48 +46,11 @@ constexpr int TARGET = 4 * 152;  // blocks that fill the GPU
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 wsum(double2 v)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    }
-    return v;
-}
+__device__ __forceinline__ double2 wsum(double2 v) { return warp_sum2(v); }
 __device__ __forceinline__ double2 ld_stream(const double2 *p) { return __ldcs(p); }
 
-// block-wide sum (all threads get the result)
-__device__ double2 block_sum(double2 v)
-{
-    __shared__ double2 red[NW];
-    __shared__ double2 tot;
-    v = wsum(v);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 s = red[0];
-        for (int q = 1; q < NW; ++q) s = zadd(s, red[q]);
-        tot = s;
-    }
-    __syncthreads();
-    return tot;
-}
-
-// true in the last block of right-hand side r to pass (resets the counter)
-__device__ bool last_of_rhs(unsigned *ticket)
-{
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        last = atomicAdd(ticket, 1u) == (unsigned)gridDim.x - 1;
-        if (last) *ticket = 0u;
-    }
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
+__device__ __forceinline__ double2 block_sum(double2 v) { return block_sum2<AT>(v); }
+__device__ __forceinline__ bool last_of_rhs(unsigned *ticket) { return last_block(ticket); }
 
 __device__ __forceinline__ double2 vload(const volatile double2 *p)
 {

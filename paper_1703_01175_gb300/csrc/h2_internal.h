@@ -175,6 +175,7 @@ struct h2_handle {
     std::vector<h2::Seg> segs_host;   // host copy of the input segments (split-bf16 packing)
     void *precond = nullptr;          // learned preconditioner (h2_precond.cu)
     void *bkrylov = nullptr;          // batched GMRES workspace (h2_bkrylov.cu)
+    void *bicgstab = nullptr;         // BiCGStab workspace (h2_bicgstab.cu)
     // captured single-RHS FP32 products, one per (x, y) pair (h2_api.cu)
     struct GraphEntry {
         const void *x;
@@ -201,6 +202,7 @@ h2_status h2_split_error_flag(h2_handle *h, int *flag);
 h2_status h2_split_set_pipeline(h2_handle *h, int on);
 void h2_free_precond(h2_handle *h);
 void h2_free_bkrylov(h2_handle *h);
+void h2_free_bicgstab(h2_handle *h);
 // z = M(v) for one c128 vector (v of unit norm or any norm); also writes c64 z32 when not NULL
 h2_status h2_apply_precond(h2_handle *h, const double2 *v, double2 *z, float2 *z32, cudaStream_t st);
 h2_status h2_run_multi_f32(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,

@@ -100,6 +100,9 @@ def lib() -> ctypes.CDLL:
     L.h2_gmres.restype = ctypes.c_int
     L.h2_gmres.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                            ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
+    L.h2_bicgstab.restype = ctypes.c_int
+    L.h2_bicgstab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                              ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
     L.h2_gmres_batched.restype = ctypes.c_int
     L.h2_gmres_batched.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                    ctypes.c_int64, ctypes.POINTER(_SolveOpts), ctypes.c_int,
@@ -359,6 +362,29 @@ class H2Matrix:
                 "precond_cycles": i.precond_cycles, "reorth_steps": i.reorth_steps} for i in infos]
         if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
             _check(status, "h2_gmres")
+        return x, out
+
+    def bicgstab(self, b, x=None, tol=1e-4, maxit=1000, refine=False, x0_given=False, arnoldi="fp64",
+                 stream=None, check=True):
+        """BiCGStab (the paper's solver) on the device. b: CUDA complex128 (n,)
+        or (n, nrhs) column-major. arnoldi selects the accumulated residual
+        product used by refine: "fp64" (FP64ACC) or "df" (DFACC).
+        Returns (x, [info dict per RHS])."""
+        import torch
+        if b.dtype != torch.complex128 or not b.is_cuda:
+            raise TypeError("b must be a CUDA complex128 tensor")
+        nrhs, ld = self._shape(b)
+        if x is None:
+            x = torch.zeros_like(b)
+        opts = _SolveOpts(float(tol), 0, int(maxit), int(bool(refine)), int(bool(x0_given)), 0, ARNOLDI[arnoldi], 0.0)
+        infos = (_SolveInfo * nrhs)()
+        st = torch.cuda.current_stream(b.device).cuda_stream if stream is None else stream
+        status = lib().h2_bicgstab(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ld,
+                                   ctypes.byref(opts), infos, ctypes.c_void_p(st))
+        out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status}
+               for i in infos]
+        if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
+            _check(status, "h2_bicgstab")
         return x, out
 
     def profile(self, x, y, iters: int = 10) -> dict:

@@ -115,7 +115,12 @@ typedef struct {
  * product is captured into a CUDA graph per (x, y) pair on first use and
  * replayed afterwards; at most 8 graphs are kept, least recently used first
  * out), "tc_pipeline=0|1" (default 1: the split-bf16 tensor-core kernel runs
- * the deepest pipeline that fits in shared memory, up to 6 stages; 0: two).
+ * the deepest pipeline that fits in shared memory, up to 6 stages; 0: two),
+ * "wait_limit=N" (polls of every bounded wait inside the tensor-core kernels,
+ * default 2^24; when one runs out the kernel waits for its copies and MMAs in
+ * flight, skips its output, frees its tensor memory and flags the handle, so
+ * that h2_device_status returns H2_ERR_TIMEOUT; 0 makes every first wait run
+ * out, which tests that path).
  */
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);

@@ -266,6 +266,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
 
     int device = 0;
     bool use_graphs = true, tc_pipeline = true;
+    uint32_t wait_limit = 1u << 24;
     if (opts) {
         const char *p = strstr(opts, "device=");
         if (p) device = atoi(p + 7);
@@ -273,12 +274,19 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         if (g) use_graphs = atoi(g + 7) != 0;
         const char *tp = strstr(opts, "tc_pipeline=");
         if (tp) tc_pipeline = atoi(tp + 12) != 0;
+        const char *wl = strstr(opts, "wait_limit=");
+        if (wl) {
+            const long long v = atoll(wl + 11);
+            if (v < 0 || v > 0xFFFFFFFFll) return arg_error("h2_load: wait_limit must lie in [0, 2^32)");
+            wait_limit = (uint32_t)v;
+        }
     }
     h2_handle *h = new (std::nothrow) h2_handle();
     if (!h) return H2_ERR_ALLOC;
     h->device = device;
     h->use_graphs = use_graphs;
     h->tc_pipeline = tc_pipeline;
+    h->wait_limit = wait_limit;
     const int32_t n = tree->n, nc = tree->n_clusters, nl = tree->n_levels;
     h->n = n;
     h->nc = nc;
@@ -716,6 +724,7 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host, int32_t
         h->d_xbuf = h->d_ybuf = nullptr;
         h->buf_bytes = 0;
         if (cudaMalloc(&h->d_xbuf, bytes) != cudaSuccess || cudaMalloc(&h->d_ybuf, bytes) != cudaSuccess) {
+            cudaGetLastError();  // clear the out-of-memory result
             set_error("h2_matvec_host: staging allocation failed");
             return H2_ERR_ALLOC;
         }
@@ -795,6 +804,7 @@ extern "C" h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len)
     cudaStream_t st = h->s_aux;
     float2 *xb = nullptr, *yb = nullptr;
     if (cudaMalloc(&xb, sizeof(float2) * h->n) != cudaSuccess || cudaMalloc(&yb, sizeof(float2) * h->n) != cudaSuccess) {
+        cudaGetLastError();  // clear the out-of-memory result
         cudaFree(xb);
         set_error("h2_autotune: allocation failed");
         return H2_ERR_ALLOC;

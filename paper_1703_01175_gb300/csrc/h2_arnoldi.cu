@@ -561,6 +561,7 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
     if (cudaMalloc(&w->block, off) != cudaSuccess || cudaMallocHost(&w->h_scal, 8 * sizeof(double) * R) != cudaSuccess ||
         cudaMallocHost(&w->h_kact, sizeof(int) * R) != cudaSuccess ||
         cudaMallocHost(&w->h_hh, sizeof(double2) * hh) != cudaSuccess) {
+        cudaGetLastError();  // an out-of-memory result must not stay behind as the last error
         arn_free(w);
         set_error("GMRES workspace allocation failed (" + std::to_string(off >> 20) + " MiB)");
         return H2_ERR_ALLOC;

@@ -261,6 +261,7 @@ static h2_status bg_get(h2_handle *h, BGWork **out)
     const size_t osc = take(sizeof(double2) * S_COUNT);
     const size_t ox = take(sizeof(float2) * n), oy = take(sizeof(float2) * n);
     if (cudaMalloc(&w->block, off) != cudaSuccess || cudaMallocHost(&w->h_sc, sizeof(double2) * S_COUNT) != cudaSuccess) {
+        cudaGetLastError();  // clear the out-of-memory result
         cudaFree(w->block);
         delete w;
         set_error("h2_bicgstab: workspace allocation failed");

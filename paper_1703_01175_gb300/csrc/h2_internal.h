@@ -83,6 +83,7 @@ struct SplitState {
     void *xhi = nullptr, *xlo = nullptr, *chi = nullptr, *clo = nullptr;  // bf16 planes
     int rcap = 0;
     int *d_err = nullptr;         // set when a bounded wait ran out
+    uint32_t wait_limit = 1u << 24;  // polls of a bounded mbarrier wait
     bool pipeline = true;         // deepest pipeline that fits (else two stages)
     size_t dyn_smem_limit = 0;    // dynamic shared memory a block may use
 };
@@ -187,6 +188,7 @@ struct h2_handle {
     uint64_t graph_clock = 0;
     bool use_graphs = true;
     bool tc_pipeline = true;          // split-bf16: deepest tensor-core pipeline that fits (else two stages)
+    uint32_t wait_limit = 1u << 24;   // polls of the tensor-core kernels' bounded waits
     cudaStream_t s_cap = nullptr;
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
 };

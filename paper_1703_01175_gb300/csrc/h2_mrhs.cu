@@ -221,6 +221,7 @@ h2_status h2_ensure_coefm(h2_handle *h, int nrhs)
     h->d_coefm = nullptr;
     h->coefm_bytes = 0;
     if (cudaMalloc(&h->d_coefm, bytes) != cudaSuccess) {
+        cudaGetLastError();  // clear the out-of-memory result
         set_error("h2_matvec: multi-RHS coefficient allocation failed");
         return H2_ERR_ALLOC;
     }

@@ -166,6 +166,7 @@ extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy,
     P->V = V;
     P->nv = nv;
     auto fail = [&](const char *what) {
+        cudaGetLastError();  // clear an out-of-memory result
         h2::set_error(std::string("h2_set_preconditioner: ") + what);
         free_state(P);
         return H2_ERR_ALLOC;

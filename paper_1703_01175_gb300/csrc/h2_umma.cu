@@ -40,7 +40,7 @@ constexpr int CPS = KST / 2;          // complex columns per stage
 constexpr int NCH = KST / 8;          // 16-byte K chunks per stage
 constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
 constexpr int XPLANE = NCH * MT * 16; // bytes of one X plane image per stage
-constexpr uint32_t kWaitLimit = 1u << 24;
+constexpr uint32_t kDrainLimit = 1u << 22;  // waits for copies and MMAs in flight after an abort
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -58,11 +58,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-// bounded wait for the phase with the given parity; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// bounded wait for the phase with the given parity; false when `limit` polls ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\n"
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
                const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
                const __nv_bfloat16 *__restrict__ xlo, int64_t nchp, int nrhs, float2 *__restrict__ out,
-               int64_t ldo, int beta_one, int nmax, int *__restrict__ err)
+               int64_t ldo, int beta_one, int nmax, int *__restrict__ err, uint32_t wait_limit)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -165,12 +165,13 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     uint64_t *full = bars;
     uint64_t *empty = bars + NS;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NS);
-    __shared__ int abort_flag;
+    __shared__ int abort_flag, issued, consumed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r0 = blockIdx.y * MT;
     if (tid == 0) {
         abort_flag = 0;
+        issued = consumed = 0;
         for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
@@ -199,10 +200,11 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             const int b = s % NS;
             const int ci[NCH] = {c0.x, c0.y, c0.z, c0.w};
             if (s + 1 < tk.nst) c0 = cq[s + 1];
-            if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1)) {
+            if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1, wait_limit)) {
                 abort_flag = 1;
                 break;
             }
+            issued = s + 1;
             uint8_t *sx = sxb + b * 2 * XPLANE;
             uint8_t *sa = sab + b * astride;
             mbar_expect_tx(&full[b], 2 * abytes + 2 * XPLANE);
@@ -218,10 +220,11 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
         const uint32_t idesc = idesc_bf16(N);
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
-            if (!mbar_wait(&full[b], (s / NS) & 1)) {
+            if (!mbar_wait(&full[b], (s / NS) & 1, wait_limit)) {
                 abort_flag = 1;
                 break;
             }
+            consumed = s + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
@@ -239,10 +242,17 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     __syncthreads();
     if (!abort_flag && tk.nst > 0) {
         const int last = tk.nst - 1;
-        if (!mbar_wait(&empty[last % NS], (last / NS) & 1)) abort_flag = 1;
+        if (tid == 0 && !mbar_wait(&empty[last % NS], (last / NS) & 1, wait_limit)) abort_flag = 1;
     }
     __syncthreads();
-    if (abort_flag && tid == 0) atomicExch(err, 1);
+    if (abort_flag && tid == 0) {
+        // a wait ran out: before the CTA releases its shared and tensor memory,
+        // let the copies of issued stages land and the committed MMAs finish
+        for (int st = consumed; st < issued; ++st) mbar_wait(&full[st % NS], (st / NS) & 1, kDrainLimit);
+        if (consumed > 0) mbar_wait(&empty[(consumed - 1) % NS], ((consumed - 1) / NS) & 1, kDrainLimit);
+        atomicExch(err, 1);
+    }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!abort_flag && tk.nst > 0) {
         const int r = r0 + warp * 32 + lane;
@@ -446,6 +456,7 @@ static h2_status split_init(h2_handle *h)
     if (h->split) return H2_OK;
     auto *S = new SplitState();
     S->pipeline = h->tc_pipeline;
+    S->wait_limit = h->wait_limit;
     // plane layouts: leaves of the tree order (near-field inputs) and cluster
     // coefficient blocks (coupling inputs), each padded to 4 complex entries
     std::vector<int32_t> leaf_pbase(h->nc, -1), coef_pbase(h->nc, -1);
@@ -583,7 +594,7 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_
     const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
 #define H2_UMMA_LAUNCH(NSV)                                                                                   \
     umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, \
-                                              beta, U.nmax, S->d_err)
+                                              beta, U.nmax, S->d_err, S->wait_limit)
     switch (ns) {
         case 6: H2_UMMA_LAUNCH(6); break;
         case 5: H2_UMMA_LAUNCH(5); break;

@@ -218,7 +218,8 @@ def _ip(a, t):
 class H2Matrix:
     """A loaded H^2 operator on one GPU (wraps an h2_handle)."""
 
-    def __init__(self, arrs: H2Arrays, device: int = 0, graphs: bool = True, tc_pipeline: bool = True):
+    def __init__(self, arrs: H2Arrays, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,
+                 wait_limit: int | None = None):
         L = lib()
         cplx = arrs.U.dtype
         if cplx not in (np.complex64, np.complex128):
@@ -243,8 +244,10 @@ class H2Matrix:
                   _ip(arrs.near_ptr, _i32p), _ip(arrs.near_col, _i32p),
                   arrs.Z.ctypes.data, _ip(arrs.Z_off, _i64p), arrs.Z.size)
         h = ctypes.c_void_p()
-        _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)}".encode(),
-                         ctypes.byref(h)), "h2_load")
+        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)}"
+        if wait_limit is not None:
+            opts += f";wait_limit={int(wait_limit)}"
+        _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), opts.encode(), ctypes.byref(h)), "h2_load")
         self._h = h
         self.device = device
         self._keep = None  # the library copied everything

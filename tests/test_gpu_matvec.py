@@ -171,3 +171,42 @@ def test_graph_replay_and_autotune(loaded):
         assert _rel(y4, y_or) <= 1e-5
     finally:
         B.close()
+
+
+def test_tensor_core_timeout_is_reported_and_context_survives(loaded):
+    """Injected timeout: with a wait limit of 0 polls every first wait of the
+    tensor-core kernels runs out; the kernels drain their copies, skip their
+    output and flag the handle, h2_device_status reports H2_ERR_TIMEOUT, and
+    the CUDA context stays usable (another handle's product is still right)."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube8")
+    A = h2.H2Matrix(c.arrays(), wait_limit=0)
+    try:
+        X = synth.random_complex(c.n, 44, cols=4)
+        A.matvec(_colmajor(X), prec="splitbf16")
+        assert A.device_status() == 6   # H2_ERR_TIMEOUT
+    finally:
+        A.close()
+    B = _mat(loaded, "cube8")
+    x = synth.random_complex(c.n, 45)
+    y = B.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+    assert B.device_status() == 0
+
+
+def test_workspace_allocation_failure_is_reported(loaded):
+    """A batched solve whose Krylov basis cannot fit in device memory returns
+    H2_ERR_ALLOC and leaves the handle usable."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube8")
+    A = _mat(loaded, "cube8")
+    R = 16384
+    B = torch.zeros(c.n, R, dtype=torch.complex128, device="cuda").t().contiguous().t()
+    B[0, :] = 1.0
+    with pytest.raises(h2.H2Error) as e:
+        # Krylov basis of 1025 x N x R complex128 entries: 413 GB, above the 288 GB of HBM
+        A.gmres_batched(B, tol=1e-4, restart=1024, maxit=10, prec="fp32")
+    assert e.value.status == 2   # H2_ERR_ALLOC
+    x = synth.random_complex(c.n, 46)
+    y = A.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+    assert _rel(y, c.oracle_matvec(x)) <= 1e-5

@@ -125,6 +125,20 @@ typedef struct {
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);
 
+/*
+ * Write a loaded operator to a file and read it back without re-validating or
+ * re-packing the blocks: the tree, the packed task and segment tables and the
+ * FP32 device matrices, followed by an FNV-1a hash of the contents (file
+ * layout in h2_api.cu). Construction of the H^2 data is the expensive step
+ * for large N; a saved operator reloads at file-read speed. h2_load_file
+ * takes the same `opts` as h2_load, checks the header, the hash and that
+ * every task and segment stays inside the matrices and vectors, and returns
+ * H2_ERR_ARG for a missing, truncated, corrupted or foreign file, before any
+ * device work. Autotuned CTA sizes are not saved (call h2_autotune again).
+ */
+h2_status h2_save(const h2_handle *h, const char *path);
+h2_status h2_load_file(const char *path, const char *opts, h2_handle **out);
+
 /* Release every device and host resource of the handle (NULL is ignored).
    Synchronises the handle's internal streams first. */
 void h2_free(h2_handle *h);

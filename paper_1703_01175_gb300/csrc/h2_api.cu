@@ -254,6 +254,97 @@ void h2_free(h2_handle *h)
     delete h;
 }
 
+// Upload the packed matrices, task and segment tables of a handle whose host
+// fields (tree, ktot, mat_elems, statistics) are set, create its streams and
+// events, and fill the phases from the task counts (order: near, leaf forward,
+// leaf expansion, couplings, upward[l], downward[l]). Frees the handle and
+// returns the status on failure.
+static h2_status upload_and_finish(h2_handle *h, int device, const float2 *mat, std::vector<Task> htasks,
+                                   std::vector<Seg> hsegs, const std::vector<int32_t> &counts)
+{
+    const int nl = h->nlev;
+    auto fail = [&](h2_status s) {
+        h2_free(h);
+        return s;
+    };
+    if ((int)counts.size() != 4 + 2 * nl) {
+        set_error("phase table does not match the tree depth");
+        return fail(H2_ERR_ARG);
+    }
+    int64_t total = 0;
+    for (int32_t c : counts) total += c;
+    if (total != (int64_t)htasks.size()) {
+        set_error("phase table does not match the task list");
+        return fail(H2_ERR_ARG);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("no CUDA device " + std::to_string(device));
+        return fail(H2_ERR_CUDA);
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return fail(H2_ERR_CUDA);
+#define H2_LOAD_CUDA(call)                                                         \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) {                                                  \
+            cudaGetLastError();                                                    \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));        \
+            return fail(e__ == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA); \
+        }                                                                          \
+    } while (0)
+    const int64_t melems = std::max<int64_t>(h->mat_elems, 32);
+    H2_LOAD_CUDA(cudaMalloc(&h->d_mat, (size_t)melems * sizeof(float2)));
+    if (mat) H2_LOAD_CUDA(cudaMemcpy(h->d_mat, mat, (size_t)melems * sizeof(float2), cudaMemcpyHostToDevice));
+    h->segs_host = hsegs;
+    H2_LOAD_CUDA(cudaMalloc(&h->d_segs, std::max<size_t>(1, hsegs.size()) * sizeof(Seg)));
+    if (!hsegs.empty())
+        H2_LOAD_CUDA(cudaMemcpy(h->d_segs, hsegs.data(), hsegs.size() * sizeof(Seg), cudaMemcpyHostToDevice));
+    H2_LOAD_CUDA(cudaMalloc(&h->d_tasks, std::max<size_t>(1, htasks.size()) * sizeof(Task)));
+    if (!htasks.empty())
+        H2_LOAD_CUDA(cudaMemcpy(h->d_tasks, htasks.data(), htasks.size() * sizeof(Task), cudaMemcpyHostToDevice));
+    H2_LOAD_CUDA(cudaMalloc(&h->d_coef, std::max<int64_t>(1, 2 * h->ktot) * sizeof(double2)));
+    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking));
+    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking));
+    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming));
+#undef H2_LOAD_CUDA
+
+    int64_t tpos = 0;
+    size_t k = 0;
+    auto fill = [&](Phase &P, const char *name) {
+        const int32_t cnt = counts[k++];
+        P.name = name;
+        P.tasks.assign(htasks.begin() + tpos, htasks.begin() + tpos + cnt);
+        P.max_mpad = P.max_ncol = 0;
+        P.elems = 0;
+        for (const Task &t : P.tasks) {
+            P.max_mpad = std::max(P.max_mpad, t.mpad);
+            P.max_ncol = std::max(P.max_ncol, t.ncol);
+            P.elems += (int64_t)t.m * t.ncol;
+        }
+        P.d_tasks = h->d_tasks + tpos;
+        tpos += cnt;
+        P.threads = choose_threads(P.tasks);
+    };
+    fill(h->near, "near");
+    fill(h->upleaf, "upleaf");
+    fill(h->leafexp, "leafexp");
+    fill(h->couple, "couple");
+    h->up.resize(nl);
+    h->down.resize(nl);
+    for (int l = 0; l < nl; ++l) fill(h->up[l], "up");
+    for (int l = 0; l < nl; ++l) fill(h->down[l], "down");
+
+    h2_stats &S = h->stats;
+    int nk = (h->near.ntask() > 0) + (h->upleaf.ntask() > 0) + (h->leafexp.ntask() > 0) + (h->couple.ntask() > 0);
+    for (int l = 0; l < nl; ++l) nk += (h->up[l].ntask() > 0) + (h->down[l].ntask() > 0);
+    S.kernels_per_matvec = nk;
+    S.device_bytes = melems * 8 + (int64_t)hsegs.size() * sizeof(Seg) + (int64_t)htasks.size() * sizeof(Task) +
+                     2 * h->ktot * 16;
+    return H2_OK;
+}
+
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out)
 {
     if (!out) return arg_error("out is NULL");
@@ -476,78 +567,19 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         return arg_error("data: non-finite entry (or entry overflowing FP32)");
     }
 
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
-        delete h;
-        set_error("no CUDA device " + std::to_string(device));
-        return H2_ERR_CUDA;
-    }
-
-    // ---- upload ---------------------------------------------------------------------
     std::vector<Task> htasks;
     std::vector<Seg> hsegs;
+    std::vector<int32_t> counts;
     htasks.reserve(ntask);
     hsegs.reserve(nseg);
-    for (auto &ph : phases)
+    for (auto &ph : phases) {
+        counts.push_back((int32_t)ph.size());
         for (auto &tb : ph) {
             htasks.push_back(tb.t);
             hsegs.insert(hsegs.end(), tb.segs.begin(), tb.segs.end());
         }
-    auto fail = [&](h2_status s) {
-        h2_free(h);
-        return s;
-    };
-    if (cudaSetDevice(device) != cudaSuccess) return fail(H2_ERR_CUDA);
-#define H2_LOAD_CUDA(call)                                                         \
-    do {                                                                           \
-        cudaError_t e__ = (call);                                                  \
-        if (e__ != cudaSuccess) {                                                  \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e__));        \
-            return fail(e__ == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA); \
-        }                                                                          \
-    } while (0)
-    H2_LOAD_CUDA(cudaMalloc(&h->d_mat, hmat.size() * sizeof(float2)));
-    H2_LOAD_CUDA(cudaMemcpy(h->d_mat, hmat.data(), hmat.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    h->mat_elems = mat_elems;
-    hmat.clear();
-    hmat.shrink_to_fit();
-    h->segs_host = hsegs;
-    H2_LOAD_CUDA(cudaMalloc(&h->d_segs, std::max<size_t>(1, hsegs.size()) * sizeof(Seg)));
-    if (!hsegs.empty())
-        H2_LOAD_CUDA(cudaMemcpy(h->d_segs, hsegs.data(), hsegs.size() * sizeof(Seg), cudaMemcpyHostToDevice));
-    H2_LOAD_CUDA(cudaMalloc(&h->d_tasks, std::max<size_t>(1, htasks.size()) * sizeof(Task)));
-    if (!htasks.empty())
-        H2_LOAD_CUDA(cudaMemcpy(h->d_tasks, htasks.data(), htasks.size() * sizeof(Task), cudaMemcpyHostToDevice));
-    H2_LOAD_CUDA(cudaMalloc(&h->d_coef, std::max<int64_t>(1, 2 * ktot) * sizeof(double2)));
-    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_aux, cudaStreamNonBlocking));
-    H2_LOAD_CUDA(cudaStreamCreateWithFlags(&h->s_cap, cudaStreamNonBlocking));
-    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
-    H2_LOAD_CUDA(cudaEventCreateWithFlags(&h->ev_near, cudaEventDisableTiming));
-
-    // ---- phases ---------------------------------------------------------------------
-    int64_t tpos = 0;
-    auto fill = [&](Phase &P, const char *name, std::vector<TaskBuild> &src) {
-        P.name = name;
-        P.tasks.clear();
-        for (auto &tb : src) {
-            P.tasks.push_back(tb.t);
-            P.max_mpad = std::max(P.max_mpad, tb.t.mpad);
-            P.max_ncol = std::max(P.max_ncol, tb.t.ncol);
-            P.elems += (int64_t)tb.t.m * tb.t.ncol;
-        }
-        P.d_tasks = h->d_tasks + tpos;
-        tpos += (int64_t)src.size();
-        P.threads = choose_threads(P.tasks);
-    };
-    fill(h->near, "near", phases[IDX_NEAR]);
-    fill(h->upleaf, "upleaf", phases[IDX_UPLEAF]);
-    fill(h->leafexp, "leafexp", phases[IDX_LEAFEXP]);
-    fill(h->couple, "couple", phases[IDX_COUPLE]);
-    h->up.resize(nl);
-    h->down.resize(nl);
-    for (int l = 0; l < nl; ++l) fill(h->up[l], "up", phases[idx_up(l)]);
-    for (int l = 0; l < nl; ++l) fill(h->down[l], "down", phases[idx_down(l)]);
-
+    }
+    phases.clear();
     h2_stats &S = h->stats;
     S.n = n;
     S.n_clusters = nc;
@@ -560,17 +592,9 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     S.transfer_elems = transfer_elems;
     S.leaf_elems = leaf_elems;
     S.max_rank = max_rank;
-    {
-        int nk = 0;
-        nk += h->near.ntask() > 0;
-        nk += h->upleaf.ntask() > 0;
-        nk += h->leafexp.ntask() > 0;
-        nk += h->couple.ntask() > 0;
-        for (int l = 0; l < nl; ++l) nk += (h->up[l].ntask() > 0) + (h->down[l].ntask() > 0);
-        S.kernels_per_matvec = nk;
-    }
-    S.device_bytes = (int64_t)std::max<int64_t>(mat_elems, 32) * 8 + (int64_t)hsegs.size() * sizeof(Seg) +
-                     (int64_t)htasks.size() * sizeof(Task) + 2 * ktot * 16;
+    h->mat_elems = mat_elems;
+    st = upload_and_finish(h, device, hmat.data(), std::move(htasks), std::move(hsegs), counts);
+    if (st != H2_OK) return st;
     *out = h;
     return H2_OK;
 }
@@ -587,6 +611,214 @@ h2_status h2_device_status(h2_handle *h)
         set_error("a bounded wait inside a tensor-core kernel ran out");
         return H2_ERR_TIMEOUT;
     }
+    return H2_OK;
+}
+
+// ---- saving and reloading a loaded operator (.h2 files) -------------------------------
+// Layout (little-endian): magic "H2PACKED", u32 version, i32 n, nc, nlev, i64 ktot,
+// mat_elems, ntask, nseg, i32 task counts per phase [4 + 2 nlev], h2_stats,
+// i32 arrays level_ptr [nlev + 1], child [2 nc], begin, size, rank, parent,
+// level, xo [nc], Task [ntask], Seg [nseg], float2 matrices [max(mat_elems, 32)],
+// u64 FNV-1a hash of everything before it.
+
+namespace {
+constexpr char kMagic[8] = {'H', '2', 'P', 'A', 'C', 'K', 'E', 'D'};
+constexpr uint32_t kVersion = 1;
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void *p, size_t n)
+    {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    }
+};
+
+struct Writer {
+    FILE *f;
+    Fnv fnv;
+    bool ok = true;
+    void put(const void *p, size_t n)
+    {
+        if (!ok || n == 0) return;
+        fnv.add(p, n);
+        ok = fwrite(p, 1, n, f) == n;
+    }
+};
+
+struct Reader {
+    FILE *f;
+    Fnv fnv;
+    bool ok = true;
+    void get(void *p, size_t n)
+    {
+        if (!ok || n == 0) return;
+        ok = fread(p, 1, n, f) == n;
+        if (ok) fnv.add(p, n);
+    }
+};
+}  // namespace
+
+h2_status h2_save(const h2_handle *h, const char *path)
+{
+    if (!h || !path) return arg_error("h2_save: NULL argument");
+    H2_CUDA(cudaSetDevice(h->device));
+    FILE *f = fopen(path, "wb");
+    if (!f) return arg_error(std::string("h2_save: cannot open ") + path);
+    Writer w{f};
+    const int32_t hdr[3] = {h->n, h->nc, h->nlev};
+    std::vector<int32_t> counts;
+    counts.push_back(h->near.ntask());
+    counts.push_back(h->upleaf.ntask());
+    counts.push_back(h->leafexp.ntask());
+    counts.push_back(h->couple.ntask());
+    for (const Phase &p : h->up) counts.push_back(p.ntask());
+    for (const Phase &p : h->down) counts.push_back(p.ntask());
+    std::vector<Task> tasks;
+    auto add = [&](const Phase &p) { tasks.insert(tasks.end(), p.tasks.begin(), p.tasks.end()); };
+    add(h->near);
+    add(h->upleaf);
+    add(h->leafexp);
+    add(h->couple);
+    for (const Phase &p : h->up) add(p);
+    for (const Phase &p : h->down) add(p);
+    const int64_t sizes[4] = {h->ktot, h->mat_elems, (int64_t)tasks.size(), (int64_t)h->segs_host.size()};
+    w.put(kMagic, 8);
+    w.put(&kVersion, 4);
+    w.put(hdr, sizeof(hdr));
+    w.put(sizes, sizeof(sizes));
+    w.put(counts.data(), counts.size() * 4);
+    w.put(&h->stats, sizeof(h2_stats));
+    for (const std::vector<int32_t> *v : {&h->level_ptr, &h->child, &h->begin, &h->size, &h->rank, &h->parent,
+                                          &h->level, &h->xo})
+        w.put(v->data(), v->size() * 4);
+    w.put(tasks.data(), tasks.size() * sizeof(Task));
+    w.put(h->segs_host.data(), h->segs_host.size() * sizeof(Seg));
+    // matrices, through a bounded host staging buffer
+    const int64_t melems = std::max<int64_t>(h->mat_elems, 32);
+    const int64_t chunk = (int64_t)1 << 25;  // 256 MB of float2
+    std::vector<float2> buf((size_t)std::min(melems, chunk));
+    for (int64_t o = 0; o < melems && w.ok; o += chunk) {
+        const int64_t m = std::min(chunk, melems - o);
+        if (cudaMemcpy(buf.data(), h->d_mat + o, (size_t)m * sizeof(float2), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            fclose(f);
+            set_error("h2_save: device read failed");
+            return H2_ERR_CUDA;
+        }
+        w.put(buf.data(), (size_t)m * sizeof(float2));
+    }
+    const uint64_t hash = w.fnv.h;
+    if (w.ok) w.ok = fwrite(&hash, 1, 8, f) == 8;
+    const bool closed = fclose(f) == 0;
+    if (!w.ok || !closed) return arg_error(std::string("h2_save: write failed: ") + path);
+    return H2_OK;
+}
+
+h2_status h2_load_file(const char *path, const char *opts, h2_handle **out)
+{
+    if (!path || !out) return arg_error("h2_load_file: NULL argument");
+    *out = nullptr;
+    int device = 0;
+    bool use_graphs = true, tc_pipeline = true;
+    uint32_t wait_limit = 1u << 24;
+    if (opts) {
+        const char *p = strstr(opts, "device=");
+        if (p) device = atoi(p + 7);
+        const char *g = strstr(opts, "graphs=");
+        if (g) use_graphs = atoi(g + 7) != 0;
+        const char *tp = strstr(opts, "tc_pipeline=");
+        if (tp) tc_pipeline = atoi(tp + 12) != 0;
+        const char *wl = strstr(opts, "wait_limit=");
+        if (wl) {
+            const long long v = atoll(wl + 11);
+            if (v < 0 || v > 0xFFFFFFFFll) return arg_error("h2_load_file: wait_limit must lie in [0, 2^32)");
+            wait_limit = (uint32_t)v;
+        }
+    }
+    FILE *f = fopen(path, "rb");
+    if (!f) return arg_error(std::string("h2_load_file: cannot open ") + path);
+    Reader r{f};
+    char magic[8];
+    uint32_t version = 0;
+    int32_t hdr[3];
+    int64_t sizes[4];
+    r.get(magic, 8);
+    r.get(&version, 4);
+    r.get(hdr, sizeof(hdr));
+    r.get(sizes, sizeof(sizes));
+    auto bad = [&](const std::string &why) {
+        fclose(f);
+        return arg_error("h2_load_file: " + why + ": " + path);
+    };
+    if (!r.ok || memcmp(magic, kMagic, 8) != 0 || version != kVersion) return bad("not a version-1 .h2 file");
+    const int32_t n = hdr[0], nc = hdr[1], nl = hdr[2];
+    if (n < 1 || nc < 1 || nl < 1 || nl > 64 || sizes[0] < 0 || sizes[1] < 0 || sizes[2] < 0 || sizes[3] < 0 ||
+        sizes[1] > ((int64_t)1 << 40) || sizes[2] > INT32_MAX || sizes[3] > INT32_MAX)
+        return bad("header out of range");
+    h2_handle *h = new (std::nothrow) h2_handle();
+    if (!h) {
+        fclose(f);
+        return H2_ERR_ALLOC;
+    }
+    h->device = device;
+    h->use_graphs = use_graphs;
+    h->tc_pipeline = tc_pipeline;
+    h->wait_limit = wait_limit;
+    h->n = n;
+    h->nc = nc;
+    h->nlev = nl;
+    h->ktot = sizes[0];
+    h->mat_elems = sizes[1];
+    std::vector<int32_t> counts(4 + 2 * nl);
+    r.get(counts.data(), counts.size() * 4);
+    r.get(&h->stats, sizeof(h2_stats));
+    h->level_ptr.resize(nl + 1);
+    h->child.resize(2 * (size_t)nc);
+    for (std::vector<int32_t> *v : {&h->begin, &h->size, &h->rank, &h->parent, &h->level, &h->xo}) v->resize(nc);
+    for (std::vector<int32_t> *v : {&h->level_ptr, &h->child, &h->begin, &h->size, &h->rank, &h->parent, &h->level,
+                                    &h->xo})
+        r.get(v->data(), v->size() * 4);
+    std::vector<Task> tasks((size_t)sizes[2]);
+    std::vector<Seg> segs((size_t)sizes[3]);
+    r.get(tasks.data(), tasks.size() * sizeof(Task));
+    r.get(segs.data(), segs.size() * sizeof(Seg));
+    std::vector<float2> mat;
+    try {
+        mat.resize((size_t)std::max<int64_t>(sizes[1], 32));
+    } catch (...) {
+        delete h;
+        fclose(f);
+        set_error("h2_load_file: host allocation failed");
+        return H2_ERR_ALLOC;
+    }
+    r.get(mat.data(), mat.size() * sizeof(float2));
+    uint64_t hash = 0;
+    const uint64_t expect = r.fnv.h;
+    const bool ok = r.ok && fread(&hash, 1, 8, f) == 8 && hash == expect;
+    fclose(f);
+    if (!ok) {
+        delete h;
+        return arg_error(std::string("h2_load_file: truncated or corrupted file: ") + path);
+    }
+    // every task and segment must stay inside the matrices and vectors
+    const int64_t melems = std::max<int64_t>(sizes[1], 32);
+    for (const Task &t : tasks)
+        if (t.m < 0 || t.mpad < t.m || t.ncol < 0 || t.mat_off < 0 || t.mat_off + (int64_t)t.mpad * t.ncol > melems ||
+            t.seg_begin < 0 || t.seg_end < t.seg_begin || t.seg_end > (int64_t)segs.size()) {
+            delete h;
+            return arg_error("h2_load_file: task table out of range");
+        }
+    for (const Seg &g : segs) {
+        const int64_t lo = g.in_off >= 0 ? g.in_off : -(int64_t)g.in_off - 1;
+        const int64_t lim = g.in_off >= 0 ? n : 2 * h->ktot;
+        if (g.n < 0 || lo + g.n > lim) {
+            delete h;
+            return arg_error("h2_load_file: segment table out of range");
+        }
+    }
+    h2_status st = upload_and_finish(h, device, mat.data(), std::move(tasks), std::move(segs), counts);
+    if (st != H2_OK) return st;
+    *out = h;
     return H2_OK;
 }
 

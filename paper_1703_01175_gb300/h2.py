@@ -100,6 +100,10 @@ def lib() -> ctypes.CDLL:
     L.h2_gmres.restype = ctypes.c_int
     L.h2_gmres.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                            ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
+    L.h2_save.restype = ctypes.c_int
+    L.h2_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    L.h2_load_file.restype = ctypes.c_int
+    L.h2_load_file.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
     L.h2_bicgstab.restype = ctypes.c_int
     L.h2_bicgstab.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                               ctypes.POINTER(_SolveOpts), ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
@@ -251,6 +255,26 @@ class H2Matrix:
         self._h = h
         self.device = device
         self._keep = None  # the library copied everything
+
+    @classmethod
+    def from_file(cls, path: str, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,
+                  wait_limit: int | None = None) -> "H2Matrix":
+        """Reload an operator written by save() (no re-validation or re-packing)."""
+        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)}"
+        if wait_limit is not None:
+            opts += f";wait_limit={int(wait_limit)}"
+        h = ctypes.c_void_p()
+        _check(lib().h2_load_file(str(path).encode(), opts.encode(), ctypes.byref(h)), "h2_load_file")
+        self = cls.__new__(cls)
+        self._h = h
+        self.device = device
+        self._keep = None
+        self.n = self.stats()["n"]
+        return self
+
+    def save(self, path: str):
+        """Write the loaded operator to `path` (see from_file)."""
+        _check(lib().h2_save(self._h, str(path).encode()), "h2_save")
 
     def close(self):
         if getattr(self, "_h", None):

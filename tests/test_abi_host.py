@@ -87,3 +87,24 @@ def test_null_arguments():
     assert h.value is None
     assert L.h2_matvec(None, None, None, 1, 1, 0, None) == h2py.H2_ERR_ARG
     L.h2_free(None)
+
+
+def test_load_file_rejects_foreign_and_corrupted_files(tmp_path):
+    """h2_load_file checks the header and the content hash before any device
+    work, so these rejections need no GPU."""
+    L = h2py.lib()
+    h = ctypes.c_void_p()
+    missing = tmp_path / "missing.h2"
+    assert L.h2_load_file(str(missing).encode(), None, ctypes.byref(h)) == h2py.H2_ERR_ARG and not h.value
+    junk = tmp_path / "junk.h2"
+    junk.write_bytes(b"not an operator file at all" * 10)
+    assert L.h2_load_file(str(junk).encode(), None, ctypes.byref(h)) == h2py.H2_ERR_ARG and not h.value
+    # a correct header with a truncated body
+    head = b"H2PACKED" + np.uint32(1).tobytes() + np.array([8, 15, 4], np.int32).tobytes() \
+        + np.array([10, 64, 3, 3], np.int64).tobytes()
+    trunc = tmp_path / "trunc.h2"
+    trunc.write_bytes(head + b"\0" * 40)
+    assert L.h2_load_file(str(trunc).encode(), None, ctypes.byref(h)) == h2py.H2_ERR_ARG and not h.value
+    assert b"truncated or corrupted" in L.h2_last_error()
+    with pytest.raises(h2py.H2Error):
+        h2py.H2Matrix.from_file(str(junk))

@@ -210,3 +210,30 @@ def test_workspace_allocation_failure_is_reported(loaded):
     x = synth.random_complex(c.n, 46)
     y = A.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
     assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+
+
+def test_save_and_reload_reproduce_products(loaded, tmp_path):
+    """An operator written by h2_save and read by h2_load_file gives bitwise
+    the same FP32 and split-bf16 products; a flipped byte is rejected."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube12")
+    A = h2.H2Matrix(c.arrays())   # fresh: the shared handles may carry autotuned CTA sizes
+    path = tmp_path / "cube12.h2"
+    A.save(str(path))
+    B = h2.H2Matrix.from_file(str(path))
+    try:
+        assert B.stats() == A.stats()
+        x = torch.from_numpy(synth.random_complex(c.n, 47).astype(np.complex64)).cuda()
+        assert torch.equal(A.matvec(x), B.matvec(x))
+        X = _colmajor(synth.random_complex(c.n, 48, cols=5))
+        assert torch.equal(A.matvec(X, prec="splitbf16"), B.matvec(X, prec="splitbf16"))
+    finally:
+        B.close()
+        A.close()
+    raw = bytearray(path.read_bytes())
+    raw[len(raw) // 2] ^= 0xFF
+    bad = tmp_path / "flipped.h2"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(h2.H2Error) as e:
+        h2.H2Matrix.from_file(str(bad))
+    assert e.value.status == 1   # H2_ERR_ARG

@@ -216,6 +216,30 @@ def run_ours(args, rank, world, local_rank):
                               "ms": e0.elapsed_time(e1) / max(1, args.steps), "status": status}), flush=True)
         return
 
+    if args.only_gmres:
+        # profiling mode: one cycle of the batched double-float solve (no other legs)
+        R = max(1, args.gmres_batch)
+        Bm = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
+        Bt = torch.from_numpy(np.asfortranarray(Bm)).to(dev).t().contiguous().t()
+        A.gmres_batched(Bt, tol=1e-12, restart=4, maxit=4, prec="splitbf16", arnoldi="df", reorth_eta=NEW_ETA,
+                        check=False)  # workspace and tensor-core images
+        torch.cuda.synchronize(dev)
+        m = args.gmres_steps
+        torch.cuda.nvtx.range_push("timed")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Xs, info = A.gmres_batched(Bt, tol=1e-12, restart=m, maxit=m, prec="splitbf16", arnoldi="df",
+                                   reorth_eta=NEW_ETA, check=False)
+        e1.record()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize(dev)
+        A.close()
+        if rank == 0:
+            print(json.dumps({"only_gmres": True, "nrhs": R, "steps": m, "workload": args.workload,
+                              "ms_per_step": e0.elapsed_time(e1) / m}), flush=True)
+        return
+
     tuning = A.autotune()
     st = A.stats()
     x_np = synth.random_complex(n, 1).astype(np.complex64)
@@ -512,6 +536,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload name (profiling uses smaller ones)")
     ap.add_argument("--only-mrhs", action="store_true",
                     help="run split-bf16 multi-RHS products only (profiling)")
+    ap.add_argument("--only-gmres", action="store_true",
+                    help="run one cycle of --gmres-steps steps of the batched double-float solve only (profiling)")
+    ap.add_argument("--gmres-steps", type=int, default=60, help="Arnoldi steps of the --only-gmres cycle")
     ap.add_argument("--only-matvec", action="store_true",
                     help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
     args = ap.parse_args()

@@ -41,7 +41,8 @@ namespace {
 
 constexpr int AT = 256;       // threads per block
 constexpr int NW = AT / 32;
-constexpr int TARGET = 4 * 152;  // blocks that fill the GPU
+constexpr int TARGET = 4 * 152;       // blocks that fill the GPU (dot pass)
+constexpr int TARGET_ROWS = 16 * 152; // blocks of the row-parallel passes (several resident per SM)
 
 __device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -331,6 +332,9 @@ __global__ void arn_widen_df(ArnDev K, const float2 *__restrict__ y32)
         w[i] = make_float4(y[i].x, y[i].y, 0.f, 0.f);
 }
 
+// Dot pass in double-float: one block per (basis column, row segment); FIRST
+// adds the pseudo-column |w|^2. (Pairing two columns per block, or four
+// entries per thread in flight, measured slower on the 32^3 cube.)
 template <bool SECOND>
 __global__ void __launch_bounds__(AT) arn_dot_df(ArnDev K, int j, int S, int seg)
 {
@@ -384,12 +388,15 @@ __global__ void __launch_bounds__(AT) arn_update_df(ArnDev K, int j, int rows)
         const float4 w0 = w[i];
         float a[4] = {w0.x, w0.z, w0.y, w0.w};
         int l = 0;
-        for (; l + 1 <= j; l += 2) {
+        for (; l + 3 <= j; l += 4) {  // four basis loads in flight
             const float4 va = ldcs4(V + (size_t)l * ldv + i), vb = ldcs4(V + (size_t)(l + 1) * ldv + i);
+            const float4 vc = ldcs4(V + (size_t)(l + 2) * ldv + i), vd = ldcs4(V + (size_t)(l + 3) * ldv + i);
             df_cmsub(a, va, hsf[l]);
             df_cmsub(a, vb, hsf[l + 1]);
+            df_cmsub(a, vc, hsf[l + 2]);
+            df_cmsub(a, vd, hsf[l + 3]);
         }
-        if (l <= j) df_cmsub(a, ldcs4(V + (size_t)l * ldv + i), hsf[l]);
+        for (; l <= j; ++l) df_cmsub(a, ldcs4(V + (size_t)l * ldv + i), hsf[l]);
         const float2 re = df_norm(a[0], a[1]), im = df_norm(a[2], a[3]);
         w[i] = make_float4(re.x, im.x, re.y, im.y);
         const double dr = df_to_d(re.x, re.y), di = df_to_d(im.x, im.y);
@@ -523,7 +530,7 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
     w->extra_cols = extra_cols;
     w->mode = mode;
     // update / residual grid: rows per block, multiple of 32
-    int nb = std::max(1, std::min((n + AT - 1) / AT, (TARGET + R - 1) / R));
+    int nb = std::max(1, std::min((n + AT - 1) / AT, (TARGET_ROWS + R - 1) / R));
     int rows = (n + nb - 1) / nb;
     rows = (rows + 31) / 32 * 32;
     w->rows = rows;
@@ -606,7 +613,10 @@ h2_status arn_set_eta(ArnWork *w, double eta)
     return H2_OK;
 }
 
-static dim3 vec_grid(const ArnWork *w) { return dim3(std::min(1024, (w->n + 255) / 256), w->R); }
+static dim3 vec_grid(const ArnWork *w)
+{
+    return dim3(std::max(1, std::min((w->n + 255) / 256, (TARGET_ROWS + w->R - 1) / w->R)), w->R);
+}
 
 h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st)
 {

@@ -118,7 +118,7 @@ def _colmajor(X):
     return torch.from_numpy(np.asfortranarray(X.astype(np.complex64))).cuda().t().contiguous().t()
 
 
-@pytest.mark.parametrize("name,R", [("cube12", 33), ("ragged", 2), ("slab", 40)])
+@pytest.mark.parametrize("name,R", [("cube12", 33), ("ragged", 2), ("slab", 40), ("cube12", 97), ("ragged", 200)])
 def test_multi_rhs_fp32_matches_oracle(loaded, name, R):
     from oracle import h2mv
     c = cases.get(name)

@@ -51,20 +51,21 @@ struct Phase {
 enum PhaseKind { PH_NEAR = 0, PH_UPLEAF, PH_UP, PH_DOWN, PH_LEAFEXP, PH_COUNT };
 
 // One tile of the split-bf16 tensor-core path (h2_umma.cu): up to 128 output
-// rows of a task, its packed matrix images and its input chunk table.
+// rows of a task (or of several tasks with the same output merged along K),
+// its packed matrix images and its input chunk table.
 struct UTask {
-    int32_t out_off;    // complex offset of the first output row
+    int32_t out_off;    // first output row: complex offset in y, or position in the bf16 plane
     int32_t m;          // complex rows in this tile (<= 128)
     int32_t n;          // real MMA N = 2 * round_up(m, 8)
-    int32_t nst;        // K stages of 32 complex columns
+    int32_t nst;        // K stages of 16 complex columns
     int64_t img_off;    // byte offset of stage 0's image (hi plane, then lo plane)
-    int32_t chunk_off;  // first entry in the chunk table (8 per stage)
+    int32_t chunk_off;  // first entry in the chunk table (4 per stage)
     int32_t pad_;
 };
 
 struct UPackInfo {
-    int32_t row0, npc, colmap_off, mpad;
-    int64_t mat_off;
+    int32_t row0, npc;    // first task row of the tile; padded columns of the task
+    int64_t colmap_off;   // first entry of the task's column table
 };
 
 struct UPhase {
@@ -74,13 +75,21 @@ struct UPhase {
     uint8_t *d_images = nullptr;
     int64_t image_bytes = 0;
     int nmax = 16;                // largest MMA N of the phase's tiles
+    int maxnst = 0;               // most K stages of a tile
 };
 
 struct SplitState {
-    UPhase near, couple;
-    int64_t np_x = 0, np_c = 0;   // padded complex lengths of the x and coefficient planes
-    int32_t *d_xpos = nullptr, *d_cpos = nullptr;  // plane position -> source index (-1: padding)
-    void *xhi = nullptr, *xlo = nullptr, *chi = nullptr, *clo = nullptr;  // bf16 planes
+    // leaf: near field and leaf expansion of every leaf (output y); upleaf and
+    // up[l]: forward transforms and upward transfer (output xh); level[l]:
+    // couplings and downward transfer of the clusters of level l (output yh)
+    UPhase leaf, upleaf;
+    std::vector<UPhase> up, level;
+    // one bf16 plane: x at positions [0, np_x), xh at [np_x, np_x + np_c), yh
+    // at [np_x + np_c, np_x + 2 np_c); nch chunks per tile, the last one zero
+    int64_t np_x = 0, np_c = 0, nch = 0;
+    int32_t *d_xpos = nullptr;    // x plane position -> index into x (-1: padding)
+    void *phi = nullptr, *plo = nullptr;
+    bool zero_y = false;          // some leaf has no task: clear y first
     int rcap = 0;
     int *d_err = nullptr;         // set when a bounded wait ran out
     uint32_t wait_limit = 1u << 24;  // polls of a bounded mbarrier wait

@@ -1,6 +1,5 @@
-// Multi-RHS near-field and coupling products on the 5th-generation tensor
-// cores (tcgen05), with operands split into two bf16 terms and FP32
-// accumulation in tensor memory.
+// Multi-RHS H2 product on the 5th-generation tensor cores (tcgen05), with
+// operands split into two bf16 terms and FP32 accumulation in tensor memory.
 //
 // For R right-hand sides a task out (m x R) = M (m x ncol) X (ncol x R) is the
 // real GEMM  D (R x 2m) = Xr (R x 2 ncol) . A2 (2m x 2 ncol)^T  with
@@ -10,16 +9,20 @@
 // Each operand is split as v = hi + lo (bf16) and D accumulates hi.hi, hi.lo and
 // lo.hi (the lo.lo term is below the FP32 rounding of the result).
 //
-// Tiles: M = 128 right-hand sides (one tile of TMEM lanes), N = 2 * m rounded
-// up to 16 (<= 256), K staged 64 bf16 (32 complex columns) at a time in
-// 128-byte-swizzled K-major shared memory. The matrix operand is pre-packed
+// Tiles: M = 128 right-hand sides (one tile of TMEM lanes), N = 2 m rounded up
+// to 16 (<= 256), K staged 32 bf16 (16 complex columns) at a time in the
+// no-swizzle K-major shared-memory layout. The matrix operand is pre-packed
 // once on the device into that exact shared-memory image and fetched with one
-// bulk asynchronous copy per stage. The right-hand-side operand lives in bf16
-// planes stored chunk-major: a chunk is 4 complex entries (16 bytes) of all
-// 128 right-hand sides of a tile, 2 KB contiguous, and every input segment
-// starts on a chunk boundary, so a stage's operand is 8 bulk copies per plane
-// into the canonical no-swizzle K-major layout (8-row core matrices 128 B
-// apart, chunks 2 KB apart).
+// bulk asynchronous copy per stage. The right-hand-side operand lives in one
+// pair of bf16 planes (hi, lo) stored chunk-major: a chunk is 4 complex
+// entries (16 bytes) of all 128 right-hand sides of a tile, 2 KB contiguous,
+// and every input segment starts on a chunk boundary, so a stage's operand is
+// 4 bulk copies per plane. The planes hold x, the coefficients xh of the
+// upward pass and yh of the downward pass; every transform writes its output
+// split straight into them (thread = right-hand side = one 16-byte chunk row),
+// so the tree passes never round-trip through FP32 buffers. The couplings of
+// a cluster and its downward transfer share one tile (their columns
+// concatenated along K), as do the near field and the leaf expansion of a leaf.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -149,9 +152,9 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
 template <int NS>
 __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
-               const uint8_t *__restrict__ images, const __nv_bfloat16 *__restrict__ xhi,
-               const __nv_bfloat16 *__restrict__ xlo, int64_t nchp, int nrhs, float2 *__restrict__ out,
-               int64_t ldo, int beta_one, int nmax, int *__restrict__ err, uint32_t wait_limit)
+               const uint8_t *__restrict__ images, __nv_bfloat16 *phi, __nv_bfloat16 *plo, int64_t nchp,
+               int nrhs, float2 *__restrict__ out, int64_t ldo, int nmax, uint32_t tcols, int *__restrict__ err,
+               uint32_t wait_limit)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -179,7 +182,8 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -192,7 +196,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
         // producer: per stage one bulk copy of the matrix image and 2 NCH bulk
         // copies of right-hand-side chunks (NCH per plane), all completing on
         // the stage's `full` barrier; chunk indices are read a stage ahead
-        const uint8_t *ph = reinterpret_cast<const uint8_t *>(xhi), *pl = reinterpret_cast<const uint8_t *>(xlo);
+        const uint8_t *ph = reinterpret_cast<const uint8_t *>(phi), *pl = reinterpret_cast<const uint8_t *>(plo);
         static_assert(NCH == 4, "one int4 of chunk indices per stage");
         const int4 *cq = reinterpret_cast<const int4 *>(chunks + tk.chunk_off);
         int4 c0 = tk.nst > 0 ? cq[0] : make_int4(-1, -1, -1, -1);
@@ -255,7 +259,9 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!abort_flag && tk.nst > 0) {
-        const int r = r0 + warp * 32 + lane;
+        // thread = right-hand side r (TMEM lane); accumulator columns 2i, 2i + 1
+        // = Re, Im of output row i
+        const int rr = warp * 32 + lane, r = r0 + rr;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
         for (int j0 = 0; j0 < N; j0 += 16) {
             uint32_t v[16];
@@ -268,18 +274,32 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
                 : "r"(tl + (uint32_t)j0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (r < nrhs) {
-                float2 *o = out + (int64_t)r * ldo + tk.out_off;
+                const int i0 = j0 >> 1;
+                if (out) {
+                    float2 *o = out + (int64_t)r * ldo + tk.out_off;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int i = j0 / 2 + q;
-                    if (i < tk.m) {
-                        float2 val = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
-                        if (beta_one) {
-                            const float2 p = o[i];
-                            val.x += p.x;
-                            val.y += p.y;
+                    for (int q = 0; q < 8; ++q)
+                        if (i0 + q < tk.m) o[i0 + q] = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
+                } else {
+                    // split into the plane: two chunks of 4 complex entries (a chunk
+                    // that starts below m may hold padding rows, whose sums are 0)
+#pragma unroll
+                    for (int hc = 0; hc < 2; ++hc) {
+                        const int ib = i0 + 4 * hc;
+                        if (ib < tk.m) {
+                            __align__(16) __nv_bfloat16 hv[8];
+                            __align__(16) __nv_bfloat16 lv[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const float f = __uint_as_float(v[8 * hc + e]);
+                                hv[e] = __float2bfloat16_rn(f);
+                                lv[e] = __float2bfloat16_rn(f - __bfloat162float(hv[e]));
+                            }
+                            const int64_t off =
+                                (((int64_t)blockIdx.y * nchp + ((tk.out_off + ib) >> 2)) * MT + rr) * 8;
+                            *reinterpret_cast<uint4 *>(phi + off) = *reinterpret_cast<const uint4 *>(hv);
+                            *reinterpret_cast<uint4 *>(plo + off) = *reinterpret_cast<const uint4 *>(lv);
                         }
-                        o[i] = val;
                     }
                 }
             }
@@ -287,14 +307,15 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
 size_t umma_ws_smem_bytes(int ns, int nmax) { return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * NCH) + 1024 + 128; }
 
-// Pack the real-expanded, bf16-split matrix images of every tile/stage.
+// Pack the real-expanded, bf16-split matrix images of every tile/stage; column
+// pc of a task starts at element colmap[colmap_off + pc] of mat (-1: padding).
 __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
-                                 const int32_t *__restrict__ colmap, const float2 *__restrict__ mat,
+                                 const int64_t *__restrict__ colmap, const float2 *__restrict__ mat,
                                  uint8_t *__restrict__ images)
 {
     const UTask tk = tasks[blockIdx.x];
@@ -307,10 +328,10 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
         const int nr = e / KST, kk = e % KST;
         const int i = pi.row0 + (nr >> 1);                 // complex row in the task matrix
         const int pc = s * CPS + (kk >> 1);                // padded complex column
-        const int c = pc < pi.npc ? colmap[pi.colmap_off + pc] : -1;
+        const int64_t c = pc < pi.npc ? colmap[pi.colmap_off + pc] : -1;   // column start in mat
         float v = 0.f;
         if (c >= 0 && (nr >> 1) < tk.m) {
-            const float2 a = mat[pi.mat_off + (int64_t)c * pi.mpad + i];
+            const float2 a = mat[c + i];
             const int part = nr & 1, comp = kk & 1;
             v = part == 0 ? (comp == 0 ? a.x : -a.y) : (comp == 0 ? a.y : a.x);
         }
@@ -322,27 +343,27 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
     }
 }
 
-// Fill chunk-major bf16 hi/lo planes: plane position d of right-hand side r
-// holds src[r * lds + pos[d]] (zero where pos[d] < 0), stored in chunk d / 4
-// of tile r / 128, row r % 128, bytes 4 (d % 4) .. + 4 (Re, Im); nchp chunks
-// per tile. A block transposes 32 positions x 32 right-hand sides through
-// shared memory, so that reads run along positions and each warp writes 32
-// consecutive 16-byte chunk rows.
+// Fill plane positions [p0, pend) of chunk-major bf16 hi/lo planes: position
+// d of right-hand side r holds src[r * lds + pos[d]] (zero where pos[d] < 0),
+// stored in chunk d / 4 of tile r / 128, row r % 128, bytes 4 (d % 4) .. + 4
+// (Re, Im); nchp chunks per tile; p0 is a multiple of 4. A block transposes
+// 32 positions x 32 right-hand sides through shared memory, so that reads run
+// along positions and each warp writes 32 consecutive 16-byte chunk rows.
 __global__ void __launch_bounds__(256)
-split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ pos, int np, int nrhs,
-                     __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
+split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ pos, int p0, int pend,
+                     int nrhs, __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
 {
     __shared__ float2 tile[32][33];
-    const int d0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int d0 = p0 + blockIdx.x * 32, r0 = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int pd = d0 + tx < np ? pos[d0 + tx] : -1;
+    const int pd = d0 + tx < pend ? pos[d0 + tx] : -1;
     for (int rr = ty; rr < 32; rr += 8) {
         const int r = r0 + rr;
         tile[rr][tx] = (pd >= 0 && r < nrhs) ? src[(int64_t)r * lds + pd] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     const int r = r0 + tx, c = (d0 >> 2) + ty;
-    if (r >= nrhs || 4 * c >= np) return;
+    if (r >= nrhs || 4 * c >= pend) return;
     __align__(16) __nv_bfloat16 hv[8];
     __align__(16) __nv_bfloat16 lv[8];
 #pragma unroll
@@ -372,31 +393,51 @@ using namespace h2;
         }                                                                             \
     } while (0)
 
-// Host side: build tiles, chunk tables and packed images of one phase.
-static h2_status build_uphase(h2_handle *h, const Phase &ph, const std::vector<Seg> &hsegs,
-                              const std::vector<int32_t> &seg_plane_base, UPhase &U)
+// A task of the tensor-core path: one output block and the handle's tasks
+// that write it, concatenated along K (their columns follow one another).
+struct MTask {
+    int32_t out_off;                 // y offset or plane position of the first output row
+    int32_t m;                       // output rows (every part has m rows)
+    std::vector<const Task *> parts;
+};
+
+// Host side: build tiles, chunk tables and packed images of one phase. seg_pos
+// gives the plane position of a segment's first entry.
+template <class SegPos>
+static h2_status build_uphase(h2_handle *h, std::vector<MTask> mts, const std::vector<Seg> &hsegs, SegPos seg_pos,
+                              UPhase &U)
 {
+    // largest tasks first, as the handle orders its own phases
+    auto work = [](const MTask &t) {
+        int64_t c = 0;
+        for (const Task *p : t.parts) c += p->ncol;
+        return (int64_t)t.m * c;
+    };
+    std::stable_sort(mts.begin(), mts.end(), [&](const MTask &a, const MTask &b) { return work(a) > work(b); });
     std::vector<UTask> tiles;
     std::vector<UPackInfo> infos;
-    std::vector<int32_t> chunks, colmap;
+    std::vector<int32_t> chunks;
+    std::vector<int64_t> colmap;
     int64_t img = 0;
-    for (const Task &t : ph.tasks) {
+    for (const MTask &t : mts) {
         // padded columns: each segment rounded up to a multiple of 4 complex entries
-        std::vector<int32_t> cm;        // padded column -> original column (-1 pad)
-        std::vector<int32_t> chunk_src; // per 4-column chunk: complex index in the bf16 plane
-        int orig = 0;
-        for (int si = t.seg_begin; si < t.seg_end; ++si) {
-            const Seg &sg = hsegs[si];
-            const int pbase = seg_plane_base[si];
-            const int np = (sg.n + 3) / 4 * 4;
-            for (int j = 0; j < np; ++j) cm.push_back(j < sg.n ? orig + j : -1);
-            for (int j = 0; j < np; j += 4) chunk_src.push_back(pbase + j);
-            orig += sg.n;
+        std::vector<int64_t> cm;        // padded column -> element offset of the column in mat (-1 pad)
+        std::vector<int32_t> chunk_src; // per 4-column chunk: plane position of its first entry
+        for (const Task *pt : t.parts) {
+            int orig = 0;
+            for (int si = pt->seg_begin; si < pt->seg_end; ++si) {
+                const Seg &sg = hsegs[si];
+                const int32_t pbase = seg_pos(sg);
+                const int np = (sg.n + 3) / 4 * 4;
+                for (int j = 0; j < np; ++j) cm.push_back(j < sg.n ? pt->mat_off + (int64_t)(orig + j) * pt->mpad : -1);
+                for (int j = 0; j < np; j += 4) chunk_src.push_back(pbase + j);
+                orig += sg.n;
+            }
         }
         const int npc = (int)cm.size();
         const int nst = (npc + CPS - 1) / CPS;
         while ((int)chunk_src.size() < nst * (CPS / 4)) chunk_src.push_back(-1);
-        const int colmap_off = (int)colmap.size();
+        const int64_t colmap_off = (int64_t)colmap.size();
         colmap.insert(colmap.end(), cm.begin(), cm.end());
         const int chunk_off = (int)chunks.size();
         chunks.insert(chunks.end(), chunk_src.begin(), chunk_src.end());
@@ -415,28 +456,30 @@ static h2_status build_uphase(h2_handle *h, const Phase &ph, const std::vector<S
             pi.row0 = row0;
             pi.npc = npc;
             pi.colmap_off = colmap_off;
-            pi.mpad = t.mpad;
-            pi.mat_off = t.mat_off;
             infos.push_back(pi);
         }
     }
     U.ntile = (int)tiles.size();
     U.image_bytes = img;
     U.nmax = 16;
-    for (auto &u : tiles) U.nmax = std::max(U.nmax, u.n);
+    U.maxnst = 0;
+    for (auto &u : tiles) {
+        U.nmax = std::max(U.nmax, u.n);
+        U.maxnst = std::max(U.maxnst, u.nst);
+    }
     if (U.ntile == 0) return H2_OK;
     UTask *d_tiles = nullptr;
     UPackInfo *d_info = nullptr;
-    int32_t *d_colmap = nullptr;
+    int64_t *d_colmap = nullptr;
     UM_CUDA(cudaMalloc(&d_tiles, tiles.size() * sizeof(UTask)));
     UM_CUDA(cudaMalloc(&d_info, infos.size() * sizeof(UPackInfo)));
-    UM_CUDA(cudaMalloc(&d_colmap, std::max<size_t>(1, colmap.size()) * sizeof(int32_t)));
+    UM_CUDA(cudaMalloc(&d_colmap, std::max<size_t>(1, colmap.size()) * sizeof(int64_t)));
     UM_CUDA(cudaMalloc(&U.d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(int32_t)));
     UM_CUDA(cudaMalloc(&U.d_images, std::max<int64_t>(16, img)));
     UM_CUDA(cudaMemcpy(d_tiles, tiles.data(), tiles.size() * sizeof(UTask), cudaMemcpyHostToDevice));
     UM_CUDA(cudaMemcpy(d_info, infos.data(), infos.size() * sizeof(UPackInfo), cudaMemcpyHostToDevice));
     if (!colmap.empty())
-        UM_CUDA(cudaMemcpy(d_colmap, colmap.data(), colmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        UM_CUDA(cudaMemcpy(d_colmap, colmap.data(), colmap.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     if (!chunks.empty())
         UM_CUDA(cudaMemcpy(U.d_chunks, chunks.data(), chunks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     int maxst = 0;
@@ -455,10 +498,11 @@ static h2_status split_init(h2_handle *h)
 {
     if (h->split) return H2_OK;
     auto *S = new SplitState();
+    h->split = S;
     S->pipeline = h->tc_pipeline;
     S->wait_limit = h->wait_limit;
-    // plane layouts: leaves of the tree order (near-field inputs) and cluster
-    // coefficient blocks (coupling inputs), each padded to 4 complex entries
+    // plane layout: leaves in tree order (x), then the coefficient blocks of
+    // the clusters (xh, then yh), each block padded to 4 complex entries
     std::vector<int32_t> leaf_pbase(h->nc, -1), coef_pbase(h->nc, -1);
     int64_t p = 0;
     std::vector<int32_t> xs, xd;
@@ -473,58 +517,88 @@ static h2_status split_init(h2_handle *h)
     }
     S->np_x = std::max<int64_t>(8, (p + 3) / 4 * 4);
     int64_t q = 0;
-    std::vector<int32_t> cs, cd;
     for (int t = 0; t < h->nc; ++t) {
         if (h->rank[t] == 0) continue;
         coef_pbase[t] = (int32_t)q;
-        for (int i = 0; i < h->rank[t]; ++i) {
-            cs.push_back(h->xo[t] + i);
-            cd.push_back((int32_t)(q + i));
-        }
         q += (h->rank[t] + 3) / 4 * 4;
     }
     S->np_c = std::max<int64_t>(8, (q + 3) / 4 * 4);
-    // plane position -> source index (-1: padding)
-    std::vector<int32_t> xpos(S->np_x, -1), cpos(S->np_c, -1);
-    for (size_t k = 0; k < xs.size(); ++k) xpos[xd[k]] = xs[k];
-    for (size_t k = 0; k < cs.size(); ++k) cpos[cd[k]] = cs[k];
-    auto up = [&](const std::vector<int32_t> &v, int32_t **d) -> h2_status {
-        UM_CUDA(cudaMalloc(d, std::max<size_t>(1, v.size()) * sizeof(int32_t)));
-        if (!v.empty()) UM_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        return H2_OK;
-    };
-    h2_status st;
-    if ((st = up(xpos, &S->d_xpos)) != H2_OK || (st = up(cpos, &S->d_cpos)) != H2_OK) {
-        h->split = S;
-        return st;
+    S->nch = (S->np_x + 2 * S->np_c) / 4 + 1;
+    if ((S->nch - 1) * 4 > INT32_MAX) {
+        set_error("split-bf16: plane positions exceed 32 bits");
+        return H2_ERR_STATE;
     }
-    // per-segment plane base of the near-field and coupling phases
+    const int32_t xh0 = (int32_t)S->np_x, yh0 = (int32_t)(S->np_x + S->np_c);
+    std::vector<int32_t> xpos(S->np_x, -1);
+    for (size_t k = 0; k < xs.size(); ++k) xpos[xd[k]] = xs[k];
+    UM_CUDA(cudaMalloc(&S->d_xpos, xpos.size() * sizeof(int32_t)));
+    UM_CUDA(cudaMemcpy(S->d_xpos, xpos.data(), xpos.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+
+    // plane position of a segment: x entries of a leaf, or a cluster's xh / yh
     const std::vector<Seg> &hsegs = h->segs_host;
     std::unordered_map<int32_t, int32_t> leaf_of_begin, cluster_of_xo;
     for (int t = 0; t < h->nc; ++t) {
         if (h->child[2 * t] < 0) leaf_of_begin[h->begin[t]] = t;
         if (h->rank[t] > 0) cluster_of_xo[h->xo[t]] = t;
     }
-    std::vector<int32_t> nbase(hsegs.size(), -1), cbase(hsegs.size(), -1);
-    auto seg_base = [&](const Phase &ph, std::vector<int32_t> &out, bool leafplane) {
-        for (const Task &t : ph.tasks)
-            for (int si = t.seg_begin; si < t.seg_end; ++si) {
-                const Seg &sg = hsegs[si];
-                if (leafplane) {
-                    // near-field segments are whole leaves: in_off = begin of the leaf
-                    const int leaf = leaf_of_begin.at(sg.in_off);
-                    out[si] = leaf_pbase[leaf];
-                } else {
-                    const int64_t off = -(int64_t)sg.in_off - 1;  // xo of the source cluster
-                    out[si] = coef_pbase[cluster_of_xo.at((int32_t)off)];
-                }
-            }
+    auto seg_pos = [&](const Seg &sg) -> int32_t {
+        if (sg.in_off >= 0) return leaf_pbase[leaf_of_begin.at(sg.in_off)];   // whole leaves
+        const int64_t off = -(int64_t)sg.in_off - 1;
+        if (off >= h->ktot) return yh0 + coef_pbase[cluster_of_xo.at((int32_t)(off - h->ktot))];
+        return xh0 + coef_pbase[cluster_of_xo.at((int32_t)off)];
     };
-    seg_base(h->near, nbase, true);
-    seg_base(h->couple, cbase, false);
-    h->split = S;
-    if ((st = build_uphase(h, h->near, hsegs, nbase, S->near)) != H2_OK) return st;
-    if ((st = build_uphase(h, h->couple, hsegs, cbase, S->couple)) != H2_OK) return st;
+    // the handle's tasks by output offset (y rows, xh or yh of a cluster)
+    auto by_out = [](const Phase &ph) {
+        std::unordered_map<int32_t, const Task *> m;
+        for (const Task &t : ph.tasks) m[t.out_off] = &t;
+        return m;
+    };
+    auto find = [](const std::unordered_map<int32_t, const Task *> &m, int32_t k) -> const Task * {
+        auto it = m.find(k);
+        return it == m.end() ? nullptr : it->second;
+    };
+    const auto near = by_out(h->near), leafexp = by_out(h->leafexp), upleaf = by_out(h->upleaf),
+               couple = by_out(h->couple);
+    std::vector<std::unordered_map<int32_t, const Task *>> up(h->nlev), down(h->nlev);
+    for (int l = 0; l < h->nlev; ++l) {
+        up[l] = by_out(h->up[l]);
+        down[l] = by_out(h->down[l]);
+    }
+    std::vector<MTask> leaf_t, upleaf_t;
+    std::vector<std::vector<MTask>> up_t(h->nlev), level_t(h->nlev);
+    for (int t = 0; t < h->nc; ++t) {
+        const int l = h->level[t];
+        const bool is_leaf = h->child[2 * t] < 0;
+        if (is_leaf) {
+            MTask m{h->begin[t], h->size[t], {}};
+            if (const Task *a = find(near, h->begin[t])) m.parts.push_back(a);
+            if (const Task *a = find(leafexp, h->begin[t])) m.parts.push_back(a);
+            if (m.parts.empty()) S->zero_y = true;
+            else leaf_t.push_back(m);
+        }
+        if (h->rank[t] == 0) continue;
+        const int32_t xo = (int32_t)h->xo[t], yo = (int32_t)(h->ktot + h->xo[t]);
+        if (is_leaf) {
+            if (const Task *a = find(upleaf, xo)) upleaf_t.push_back({xh0 + coef_pbase[t], h->rank[t], {a}});
+        } else if (const Task *a = find(up[l], xo)) {
+            up_t[l].push_back({xh0 + coef_pbase[t], h->rank[t], {a}});
+        }
+        MTask m{yh0 + coef_pbase[t], h->rank[t], {}};
+        if (const Task *a = find(couple, yo)) m.parts.push_back(a);
+        if (const Task *a = find(down[l], yo)) m.parts.push_back(a);
+        if (!m.parts.empty()) level_t[l].push_back(m);
+    }
+    h2_status st;
+    if ((st = build_uphase(h, leaf_t, hsegs, seg_pos, S->leaf)) != H2_OK) return st;
+    if ((st = build_uphase(h, upleaf_t, hsegs, seg_pos, S->upleaf)) != H2_OK) return st;
+    S->up.resize(h->nlev);
+    S->level.resize(h->nlev);
+    for (int l = 0; l < h->nlev; ++l) {
+        if ((st = build_uphase(h, up_t[l], hsegs, seg_pos, S->up[l])) != H2_OK) return st;
+        if ((st = build_uphase(h, level_t[l], hsegs, seg_pos, S->level[l])) != H2_OK) return st;
+    }
+    int nmax = std::max(S->leaf.nmax, S->upleaf.nmax);
+    for (int l = 0; l < h->nlev; ++l) nmax = std::max(nmax, std::max(S->up[l].nmax, S->level[l].nmax));
     {
         // dynamic shared memory limit = opt-in per-block maximum minus the kernels' static shared memory
         int optin = 0;
@@ -532,7 +606,7 @@ static h2_status split_init(h2_handle *h)
         cudaFuncAttributes fa{};
         UM_CUDA(cudaFuncGetAttributes(&fa, umma_ws_kernel<2>));
         S->dyn_smem_limit = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        if (umma_ws_smem_bytes(2, std::max(S->near.nmax, S->couple.nmax)) > S->dyn_smem_limit) {
+        if (umma_ws_smem_bytes(2, nmax) > S->dyn_smem_limit) {
             set_error("split-bf16: two pipeline stages of the widest tile exceed shared memory");
             return H2_ERR_STATE;
         }
@@ -552,49 +626,47 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
 {
     SplitState *S = h->split;
     if (rpad <= S->rcap) return H2_OK;
-    cudaFree(S->xhi);
-    cudaFree(S->xlo);
-    cudaFree(S->chi);
-    cudaFree(S->clo);
-    S->xhi = S->xlo = S->chi = S->clo = nullptr;
+    cudaFree(S->phi);
+    cudaFree(S->plo);
+    S->phi = S->plo = nullptr;
     S->rcap = 0;
-    // chunk-major planes: per tile of 128 right-hand sides, np / 4 chunks of
-    // 2 KB plus one zero chunk (np is a multiple of 4)
-    const size_t bx = (size_t)rpad * (S->np_x / 4 + 1) * 16;
-    const size_t bc = (size_t)rpad * (S->np_c / 4 + 1) * 16;
-    if (cudaMalloc(&S->xhi, bx) != cudaSuccess || cudaMalloc(&S->xlo, bx) != cudaSuccess ||
-        cudaMalloc(&S->chi, bc) != cudaSuccess || cudaMalloc(&S->clo, bc) != cudaSuccess) {
+    // chunk-major: per tile of 128 right-hand sides, nch chunks of 2 KB
+    const size_t bytes = (size_t)rpad * S->nch * 16;
+    if (cudaMalloc(&S->phi, bytes) != cudaSuccess || cudaMalloc(&S->plo, bytes) != cudaSuccess) {
+        cudaGetLastError();
         set_error("split-bf16 plane allocation failed");
         return H2_ERR_ALLOC;
     }
-    // padding entries and the zero chunks stay zero: the scatter kernels never write them
-    UM_CUDA(cudaMemset(S->xhi, 0, bx));
-    UM_CUDA(cudaMemset(S->xlo, 0, bx));
-    UM_CUDA(cudaMemset(S->chi, 0, bc));
-    UM_CUDA(cudaMemset(S->clo, 0, bc));
+    // entries that no kernel writes stay zero: the zero chunk, padding between
+    // blocks, and the xh / yh of clusters that no task writes
+    UM_CUDA(cudaMemset(S->phi, 0, bytes));
+    UM_CUDA(cudaMemset(S->plo, 0, bytes));
     S->rcap = rpad;
     return H2_OK;
 }
 
-// Deepest pipeline that fits in shared memory (two stages when the pipeline
-// option is off).
-static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_bfloat16 *phi,
-                               const __nv_bfloat16 *plo, int64_t nchp, int nrhs, float2 *out, int64_t ldo,
-                               int beta, cudaStream_t st)
+// Deepest pipeline that fits in shared memory and that the phase's longest
+// tile can use (two stages when the pipeline option is off); tensor memory
+// columns: the power of two that holds the widest accumulator.
+static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, float2 *out, int64_t ldo,
+                               cudaStream_t st)
 {
     if (U.ntile == 0) return cudaSuccess;
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
     int ns = 2;
     if (S->pipeline)
-        for (int c = 6; c > 2; --c)
+        for (int c = std::min(6, std::max(2, U.maxnst)); c > 2; --c)
             if (umma_ws_smem_bytes(c, U.nmax) <= S->dyn_smem_limit) {
                 ns = c;
                 break;
             }
+    uint32_t tcols = 32;
+    while ((int)tcols < U.nmax) tcols <<= 1;
     const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
-#define H2_UMMA_LAUNCH(NSV)                                                                                   \
-    umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, nchp, nrhs, out, ldo, \
-                                              beta, U.nmax, S->d_err, S->wait_limit)
+    __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
+#define H2_UMMA_LAUNCH(NSV)                                                                                  \
+    umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, S->nch, nrhs, out, \
+                                              ldo, U.nmax, tcols, S->d_err, S->wait_limit)
     switch (ns) {
         case 6: H2_UMMA_LAUNCH(6); break;
         case 5: H2_UMMA_LAUNCH(5); break;
@@ -606,28 +678,29 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, const __nv_
     return cudaGetLastError();
 }
 
-static inline __nv_bfloat16 *bf(void *p) { return reinterpret_cast<__nv_bfloat16 *>(p); }
-
 void h2_free_split(h2_handle *h)
 {
     SplitState *S = h->split;
     if (!S) return;
-    for (UPhase *U : {&S->near, &S->couple}) {
+    std::vector<UPhase *> all = {&S->leaf, &S->upleaf};
+    for (UPhase &U : S->up) all.push_back(&U);
+    for (UPhase &U : S->level) all.push_back(&U);
+    for (UPhase *U : all) {
         cudaFree(U->d_tasks);
         cudaFree(U->d_chunks);
         cudaFree(U->d_images);
     }
     cudaFree(S->d_xpos);
-    cudaFree(S->d_cpos);
-    cudaFree(S->xhi);
-    cudaFree(S->xlo);
-    cudaFree(S->chi);
-    cudaFree(S->clo);
+    cudaFree(S->phi);
+    cudaFree(S->plo);
     cudaFree(S->d_err);
     delete S;
     h->split = nullptr;
 }
 
+// Product for R right-hand sides: x is split into the plane once; every
+// transform writes its output coefficients into the plane, split, where the
+// next level's tiles read them; only the leaf phase writes FP32 (y).
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st)
 {
@@ -636,35 +709,18 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     SplitState *S = h->split;
     const int rpad = (nrhs + MT - 1) / MT * MT;
     if ((s = ensure_planes(h, rpad)) != H2_OK) return s;
-    if ((s = h2_ensure_coefm(h, nrhs)) != H2_OK) return s;
-    if ((s = h2_ensure_colidx(h)) != H2_OK) return s;
-    const int64_t ldc = std::max<int64_t>(2, 2 * h->ktot);
-    float2 *coef = reinterpret_cast<float2 *>(h->d_coefm);
-    const float2 *mat = h->d_mat;
-    const int64_t nchx = S->np_x / 4 + 1, nchc = S->np_c / 4 + 1;  // chunks per tile, zero chunk last
-    UM_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * ldc * nrhs, st));
-    {
-        dim3 g((unsigned)((S->np_x + 31) / 32), (nrhs + 31) / 32);
-        split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xpos, (int)S->np_x, nrhs, bf(S->xhi), bf(S->xlo), nchx);
-        UM_CUDA(cudaGetLastError());
-    }
-    UM_CUDA(cudaEventRecord(h->ev_fork, st));
-    UM_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
-    UM_CUDA(launch_umma(S->near, S, bf(S->xhi), bf(S->xlo), nchx, nrhs, y, ldy, 0, h->s_aux));
-    UM_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
-    UM_CUDA(launch_phase_mrhs_f32(h->upleaf, mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
-    for (int l = h->nlev - 1; l >= 0; --l)
-        UM_CUDA(launch_phase_mrhs_f32(h->up[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 0, st));
-    {
-        dim3 g((unsigned)((S->np_c + 31) / 32), (nrhs + 31) / 32);
-        split_scatter_kernel<<<g, 256, 0, st>>>(coef, ldc, S->d_cpos, (int)S->np_c, nrhs, bf(S->chi), bf(S->clo), nchc);
-        UM_CUDA(cudaGetLastError());
-    }
-    UM_CUDA(launch_umma(S->couple, S, bf(S->chi), bf(S->clo), nchc, nrhs, coef, ldc, 0, st));
-    for (int l = 0; l < h->nlev; ++l)
-        UM_CUDA(launch_phase_mrhs_f32(h->down[l], mat, x, ldx, coef, ldc, coef, ldc, nrhs, 1, st));
-    UM_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
-    UM_CUDA(launch_phase_mrhs_f32(h->leafexp, mat, x, ldx, coef, ldc, y, ldy, nrhs, 1, st));
+    dim3 g((unsigned)((S->np_x + 31) / 32), (nrhs + 31) / 32);
+    split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xpos, 0, (int)S->np_x, nrhs,
+                                            reinterpret_cast<__nv_bfloat16 *>(S->phi),
+                                            reinterpret_cast<__nv_bfloat16 *>(S->plo), S->nch);
+    UM_CUDA(cudaGetLastError());
+    // upward pass: forward transforms of the leaves, then level by level
+    UM_CUDA(launch_umma(S->upleaf, S, nrhs, nullptr, 0, st));
+    for (int l = h->nlev - 1; l >= 0; --l) UM_CUDA(launch_umma(S->up[l], S, nrhs, nullptr, 0, st));
+    // couplings with the downward transfer from the parent, root to leaves
+    for (int l = 0; l < h->nlev; ++l) UM_CUDA(launch_umma(S->level[l], S, nrhs, nullptr, 0, st));
+    if (S->zero_y) UM_CUDA(cudaMemset2DAsync(y, sizeof(float2) * ldy, 0, sizeof(float2) * h->n, nrhs, st));
+    UM_CUDA(launch_umma(S->leaf, S, nrhs, y, ldy, st));
     return H2_OK;
 }
 

@@ -104,6 +104,7 @@ def construct_cached(w):
 # keeps w' orthogonal to the basis to about u / eta (Daniel et al. 1976), 10 u
 # here; the plain solve keeps the classical eta = 1/sqrt(2).
 NEW_ETA = 0.1
+NEW_ARNOLDI = "fp32"  # c64 basis, FP32 products with compensated sums, FP64 reductions
 
 
 def build_workload(name: str):
@@ -217,19 +218,19 @@ def run_ours(args, rank, world, local_rank):
         return
 
     if args.only_gmres:
-        # profiling mode: one cycle of the batched double-float solve (no other legs)
+        # profiling mode: one cycle of the batched solve (no other legs)
         R = max(1, args.gmres_batch)
         Bm = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
         Bt = torch.from_numpy(np.asfortranarray(Bm)).to(dev).t().contiguous().t()
-        A.gmres_batched(Bt, tol=1e-12, restart=4, maxit=4, prec="splitbf16", arnoldi="df", reorth_eta=NEW_ETA,
-                        check=False)  # workspace and tensor-core images
+        A.gmres_batched(Bt, tol=1e-12, restart=4, maxit=4, prec="splitbf16", arnoldi=args.arnoldi,
+                        reorth_eta=NEW_ETA, check=False)  # workspace and tensor-core images
         torch.cuda.synchronize(dev)
         m = args.gmres_steps
         torch.cuda.nvtx.range_push("timed")
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        Xs, info = A.gmres_batched(Bt, tol=1e-12, restart=m, maxit=m, prec="splitbf16", arnoldi="df",
+        Xs, info = A.gmres_batched(Bt, tol=1e-12, restart=m, maxit=m, prec="splitbf16", arnoldi=args.arnoldi,
                                    reorth_eta=NEW_ETA, check=False)
         e1.record()
         torch.cuda.nvtx.range_pop()
@@ -237,7 +238,7 @@ def run_ours(args, rank, world, local_rank):
         A.close()
         if rank == 0:
             print(json.dumps({"only_gmres": True, "nrhs": R, "steps": m, "workload": args.workload,
-                              "ms_per_step": e0.elapsed_time(e1) / m}), flush=True)
+                              "arnoldi": args.arnoldi, "ms_per_step": e0.elapsed_time(e1) / m}), flush=True)
         return
 
     tuning = A.autotune()
@@ -355,7 +356,7 @@ def run_ours(args, rank, world, local_rank):
         mr["speedup_vs_single_rhs_fp32"] = (ms * R) / mr["splitbf16"]["ms"]
         mr["tc_entries"] = tc_entries
 
-    # "new" solve: R right-hand sides in lockstep, split-bf16 tensor-core products, double-float Arnoldi and
+    # "new" solve: R right-hand sides in lockstep, split-bf16 tensor-core products, Arnoldi on a c64 basis and
     # double-float-accumulated restart residuals; compared per right-hand side with plain single-RHS GMRES
     # (FP32 products, FP64 Arnoldi, FP64-accumulated restart residuals)
     if args.gmres_batch > 0:
@@ -383,7 +384,7 @@ def run_ours(args, rank, world, local_rank):
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         Xs, info = A.gmres_batched(Bt, tol=w.tol, restart=m_new, maxit=4000, refine=True, prec="splitbf16",
-                                   arnoldi="df", reorth_eta=NEW_ETA)
+                                   arnoldi=NEW_ARNOLDI, reorth_eta=NEW_ETA)
         g1.record(stream)
         torch.cuda.synchronize(dev)
         t_new = g0.elapsed_time(g1)
@@ -393,9 +394,10 @@ def run_ours(args, rank, world, local_rank):
                              "mean_iterations": float(np.mean([i["iterations"] for i in info])),
                              "mean_reorth_steps": float(np.mean([i["reorth_steps"] for i in info])),
                              "reorth_eta": NEW_ETA,
-                             "products": "split-bf16 tensor cores; double-float Gram-Schmidt (FP32 pipes, FP64 "
-                                         "reductions) with selective reorthogonalisation; double-float-accumulated "
-                                         "restart residuals"}
+                             "products": "split-bf16 tensor cores; Gram-Schmidt on a c64 basis (FP32 products, "
+                                         "compensated per-thread sums, FP64 reductions) with selective "
+                                         "reorthogonalisation; double-float-accumulated restart residuals",
+                             "arnoldi": NEW_ARNOLDI}
         gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
 
     # learned preconditioner (shipped weights, trained by train_precond on the 16^3 cube): flexible
@@ -539,6 +541,8 @@ def main():
     ap.add_argument("--only-gmres", action="store_true",
                     help="run one cycle of --gmres-steps steps of the batched double-float solve only (profiling)")
     ap.add_argument("--gmres-steps", type=int, default=60, help="Arnoldi steps of the --only-gmres cycle")
+    ap.add_argument("--arnoldi", default="fp32", choices=["fp64", "df", "fp32"],
+                    help="Arnoldi arithmetic of the --only-gmres cycle")
     ap.add_argument("--only-matvec", action="store_true",
                     help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
     args = ap.parse_args()

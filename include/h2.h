@@ -251,7 +251,13 @@ typedef struct {
                           and compensated sums, Ogita-Rump-Oishi 2005) on the
                           FP32 pipes, with FP64 reductions, norms and least
                           squares. GB300 issues FP64 at about 1/58 of the FP32
-                          rate. 1 is not available with precond = 1. */
+                          rate. 2 = c64 basis and work vector (8 bytes per
+                          entry, half the traffic of 0 and 1), FP32 products
+                          summed with compensation, FP64 reductions, norms and
+                          least squares; the stored vectors carry FP32
+                          rounding, so tolerances well above 1e-7 only.
+                          1 and 2 are not available with precond = 1; with
+                          refine, 1 and 2 use the DFACC residual, 0 FP64ACC. */
     double reorth_eta; /* selective reorthogonalisation threshold eta in [0, 1]:
                           a second Gram-Schmidt projection when the first
                           leaves |w'| < eta |w| (Daniel, Gragg, Kaufman &

@@ -482,6 +482,215 @@ __global__ void arn_xupdate_df(ArnDev K, double2 *__restrict__ x, int64_t ldx)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single-precision basis. Basis and work vector are stored as c64: 8 bytes
+// per entry, half the traffic of the FP64 and double-float modes in both
+// O(j n) passes. Products are FP32; each thread sums them in groups of four
+// (plain FMAs) and adds every group into a compensated running sum (TwoSum),
+// so its error stays a few units of FP32 rounding however long the sum is.
+// Per-thread sums are converted to FP64 before any cross-thread reduction, so
+// coefficients, norms and the least squares stay FP64, as in the other modes.
+// The stored vectors carry FP32 rounding (2^-24 relative), which bounds the
+// accuracy of the Arnoldi relation near 1e-7: the mode is for tolerances far
+// above that (split-bf16 products are themselves accurate to about 1e-5).
+
+__device__ __forceinline__ float2 ldcs2(const float2 *p) { return __ldcs(p); }
+
+// (s, c) += t, compensated
+__device__ __forceinline__ void csum(float &s, float &c, float t)
+{
+    float u, q;
+    two_sum(s, t, u, q);
+    s = u;
+    c = __fadd_rn(c, q);
+}
+
+// Dot pass with a c64 basis: one block per (basis column, row segment), four
+// entries per thread in flight; FIRST adds the pseudo-column |w|^2.
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_dot_f32(ArnDev K, int j, int S, int seg)
+{
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const int l = blockIdx.x / S, s = blockIdx.x - l * S;
+    const int i0 = s * seg, i1 = min(K.n, i0 + seg);
+    const float2 *w = reinterpret_cast<const float2 *>(K.w) + (size_t)r * K.n;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    if (l <= j) {
+        const float2 *Vl = reinterpret_cast<const float2 *>(K.V) + ((size_t)l * K.R + r) * K.n;
+        int i = i0 + threadIdx.x;
+        for (; i + 3 * AT < i1; i += 4 * AT) {
+            const float2 v0 = ldcs2(Vl + i), v1 = ldcs2(Vl + i + AT), v2 = ldcs2(Vl + i + 2 * AT),
+                         v3 = ldcs2(Vl + i + 3 * AT);
+            const float2 w0 = w[i], w1 = w[i + AT], w2 = w[i + 2 * AT], w3 = w[i + 3 * AT];
+            float tr = v0.x * w0.x;   // conj(v) w, four entries
+            tr = fmaf(v0.y, w0.y, tr);
+            tr = fmaf(v1.x, w1.x, tr);
+            tr = fmaf(v1.y, w1.y, tr);
+            tr = fmaf(v2.x, w2.x, tr);
+            tr = fmaf(v2.y, w2.y, tr);
+            tr = fmaf(v3.x, w3.x, tr);
+            tr = fmaf(v3.y, w3.y, tr);
+            float ti = v0.x * w0.y;
+            ti = fmaf(-v0.y, w0.x, ti);
+            ti = fmaf(v1.x, w1.y, ti);
+            ti = fmaf(-v1.y, w1.x, ti);
+            ti = fmaf(v2.x, w2.y, ti);
+            ti = fmaf(-v2.y, w2.x, ti);
+            ti = fmaf(v3.x, w3.y, ti);
+            ti = fmaf(-v3.y, w3.x, ti);
+            csum(sr, cr, tr);
+            csum(si, ci, ti);
+        }
+        for (; i < i1; i += AT) {
+            const float2 v = ldcs2(Vl + i), x = w[i];
+            csum(sr, cr, fmaf(v.y, x.y, v.x * x.x));
+            csum(si, ci, fmaf(-v.y, x.x, v.x * x.y));
+        }
+    } else {  // FIRST only: |w|^2 over the segment
+        for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+            const float2 x = w[i];
+            csum(sr, cr, fmaf(x.y, x.y, x.x * x.x));
+        }
+    }
+    const double2 tot = block_sum(make_double2(df_to_d(sr, cr), df_to_d(si, ci)));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 2 : 0))) return;
+    const int ncols = SECOND ? j + 1 : j + 2;
+    reduce_columns(part, ncols, S, (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2));
+}
+
+// w -= V h with a c64 basis: four basis columns per group (plain FMAs, four
+// loads in flight), groups added compensated; |w'|^2 in FP64. Dynamic shared
+// memory: m + 2 float2 entries.
+template <bool SECOND>
+__global__ void __launch_bounds__(AT) arn_update_f32(ArnDev K, int j, int rows)
+{
+    extern __shared__ float2 hs32[];
+    const int r = blockIdx.y;
+    if (SECOND && K.scal[8 * r + 3] == 0.0) return;
+    const double2 *h = (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2);
+    for (int l = threadIdx.x; l <= j; l += AT) hs32[l] = make_float2((float)h[l].x, (float)h[l].y);
+    __syncthreads();
+    const int i0 = blockIdx.x * rows, i1 = min(K.n, i0 + rows);
+    float2 *w = reinterpret_cast<float2 *>(K.w) + (size_t)r * K.n;
+    const float2 *V = reinterpret_cast<const float2 *>(K.V) + (size_t)r * K.n;
+    const size_t ldv = (size_t)K.R * K.n;
+    double nrm = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += AT) {
+        const float2 w0 = w[i];
+        float sr = w0.x, cr = 0.f, si = w0.y, ci = 0.f;
+        int l = 0;
+        for (; l + 3 <= j; l += 4) {
+            const float2 va = ldcs2(V + (size_t)l * ldv + i), vb = ldcs2(V + (size_t)(l + 1) * ldv + i);
+            const float2 vc = ldcs2(V + (size_t)(l + 2) * ldv + i), vd = ldcs2(V + (size_t)(l + 3) * ldv + i);
+            const float2 ha = hs32[l], hb = hs32[l + 1], hc = hs32[l + 2], hd = hs32[l + 3];
+            float tr = va.y * ha.y;   // -Re(v h), four columns
+            tr = fmaf(-va.x, ha.x, tr);
+            tr = fmaf(-vb.x, hb.x, tr);
+            tr = fmaf(vb.y, hb.y, tr);
+            tr = fmaf(-vc.x, hc.x, tr);
+            tr = fmaf(vc.y, hc.y, tr);
+            tr = fmaf(-vd.x, hd.x, tr);
+            tr = fmaf(vd.y, hd.y, tr);
+            float ti = -va.x * ha.y;  // -Im(v h)
+            ti = fmaf(-va.y, ha.x, ti);
+            ti = fmaf(-vb.x, hb.y, ti);
+            ti = fmaf(-vb.y, hb.x, ti);
+            ti = fmaf(-vc.x, hc.y, ti);
+            ti = fmaf(-vc.y, hc.x, ti);
+            ti = fmaf(-vd.x, hd.y, ti);
+            ti = fmaf(-vd.y, hd.x, ti);
+            csum(sr, cr, tr);
+            csum(si, ci, ti);
+        }
+        for (; l <= j; ++l) {
+            const float2 v = ldcs2(V + (size_t)l * ldv + i), hh = hs32[l];
+            csum(sr, cr, fmaf(v.y, hh.y, -v.x * hh.x));
+            csum(si, ci, fmaf(-v.y, hh.x, -v.x * hh.y));
+        }
+        const float2 o = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
+        w[i] = o;
+        nrm = fma((double)o.x, (double)o.x, nrm);
+        nrm = fma((double)o.y, (double)o.y, nrm);
+    }
+    const double2 tot = block_sum(make_double2(nrm, 0.0));
+    double2 *part = K.part + (size_t)r * K.np;
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (!last_of_rhs(K.ticket + 8 * r + (SECOND ? 3 : 1))) return;
+    double sum = 0.0;
+    const volatile double2 *p = part;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += AT) sum += p[b].x;
+    const double nw2 = block_sum(make_double2(sum, 0.0)).x;
+    if (threadIdx.x != 0) return;
+    if (!SECOND) {
+        const double rho = K.h1[(size_t)r * (K.m + 2) + j + 1].x;
+        const bool again = !(nw2 >= K.eta2 * rho);
+        K.scal[8 * r + 3] = again ? 1.0 : 0.0;
+        if (again) return;
+    }
+    K.scal[8 * r] = sqrt(nw2);
+}
+
+// v_{jn} = w / beta (c64); x32 = the same vector
+__global__ void arn_normalize_f32(ArnDev K, int jn, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    float2 *Vn = reinterpret_cast<float2 *>(K.V) + ((size_t)jn * K.R + r) * K.n;
+    const float2 *w = reinterpret_cast<const float2 *>(K.w) + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const float2 v = w[i];
+        const float2 q = make_float2((float)(v.x * inv), (float)(v.y * inv));
+        Vn[i] = q;
+        x[i] = q;
+    }
+}
+
+// v_0 = rr / beta (c64); x32 = the same vector
+__global__ void arn_start_f32(ArnDev K, const double2 *__restrict__ rr, float2 *__restrict__ x32)
+{
+    const int r = blockIdx.y;
+    const double beta = K.scal[8 * r];
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    float2 *V0 = reinterpret_cast<float2 *>(K.V) + (size_t)r * K.n;
+    const double2 *v = rr + (size_t)r * K.n;
+    float2 *x = x32 + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        const float2 q = make_float2((float)(v[i].x * inv), (float)(v[i].y * inv));
+        V0[i] = q;
+        x[i] = q;
+    }
+}
+
+// x += V y (c128 x, c64 basis, FP64 FMAs: once per restart cycle)
+__global__ void arn_xupdate_f32(ArnDev K, double2 *__restrict__ x, int64_t ldx)
+{
+    extern __shared__ double2 ys64[];
+    const int r = blockIdx.y;
+    const int k = K.kact[r];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) ys64[l] = K.h1[(size_t)r * (K.m + 2) + l];
+    __syncthreads();
+    if (k == 0) return;
+    const size_t ldb = (size_t)K.R * K.n;
+    const float2 *V = reinterpret_cast<const float2 *>(K.V) + (size_t)r * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        double2 a = x[(size_t)r * ldx + i];
+        for (int l = 0; l < k; ++l) {
+            const float2 v = V[(size_t)l * ldb + i];
+            const double2 y = ys64[l];
+            a.x = fma((double)v.x, y.x, a.x);
+            a.x = fma(-(double)v.y, y.y, a.x);
+            a.y = fma((double)v.x, y.y, a.y);
+            a.y = fma((double)v.y, y.x, a.y);
+        }
+        x[(size_t)r * ldx + i] = a;
+    }
+}
+
 // segments of the dot pass at step j: enough blocks to fill the GPU
 void dot_split(int n, int R, int j, int *S, int *seg)
 {
@@ -521,8 +730,9 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
     if (w && w->n == n && w->m == m && w->R == R && w->extra_cols == extra_cols && w->mode == mode) return H2_OK;
     arn_free(w);
     *slot = nullptr;
-    if (mode != ARN_FP64 && mode != ARN_DF) return (set_error("GMRES: unknown Arnoldi arithmetic"), H2_ERR_ARG);
-    if (mode == ARN_DF && extra_cols) return (set_error("GMRES: double-float Arnoldi has no flexible variant"), H2_ERR_ARG);
+    if (mode != ARN_FP64 && mode != ARN_DF && mode != ARN_F32) return (set_error("GMRES: unknown Arnoldi arithmetic"), H2_ERR_ARG);
+    if (mode != ARN_FP64 && extra_cols)
+        return (set_error("GMRES: only the FP64 Arnoldi has a flexible variant"), H2_ERR_ARG);
     w = new ArnWork();
     w->n = n;
     w->m = m;
@@ -553,9 +763,10 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
         return o;
     };
     const size_t hh = (size_t)2 * R * (m + 2);  // h1 rows, then h2 rows
-    const size_t oV = take(sizeof(double2) * (size_t)n * (m + 1) * R);
+    const size_t ventry = mode == ARN_F32 ? sizeof(float2) : sizeof(double2);   // bytes per basis entry
+    const size_t oV = take(ventry * (size_t)n * (m + 1) * R);
     const size_t oZ = extra_cols ? take(sizeof(double2) * (size_t)n * extra_cols * R) : 0;
-    const size_t ow = take(sizeof(double2) * (size_t)n * R);
+    const size_t ow = take(ventry * (size_t)n * R);
     const size_t op = take(sizeof(double2) * (size_t)np * R);
     const size_t ot = take(sizeof(unsigned) * 8 * R);
     const size_t oh = take(sizeof(double2) * hh);
@@ -629,6 +840,8 @@ h2_status arn_start(ArnWork *w, cudaStream_t st)
 {
     if (w->mode == ARN_DF)
         arn_start_df<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
+    else if (w->mode == ARN_F32)
+        arn_start_f32<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
     else
         arn_start<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
     ARNC(cudaGetLastError());
@@ -707,6 +920,13 @@ h2_status arn_step(ArnWork *w, int j, cudaStream_t st)
         arn_dot_df<true><<<g2, AT, 0, st>>>(K, j, S, seg);
         arn_update_df<true><<<gu, AT, smem, st>>>(K, j, w->rows);
         arn_normalize_df<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+    } else if (w->mode == ARN_F32) {
+        ARNC(cudaMemcpyAsync(K.w, w->y32, sizeof(float2) * (size_t)w->n * w->R, cudaMemcpyDeviceToDevice, st));
+        arn_dot_f32<false><<<g1, AT, 0, st>>>(K, j, S, seg);
+        arn_update_f32<false><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_dot_f32<true><<<g2, AT, 0, st>>>(K, j, S, seg);
+        arn_update_f32<true><<<gu, AT, smem, st>>>(K, j, w->rows);
+        arn_normalize_f32<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
     } else {
         arn_widen<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
         arn_dot<false><<<g1, AT, 0, st>>>(K, j, S, seg);
@@ -751,6 +971,8 @@ h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, 
     ARNC(cudaMemcpyAsync(w->K.kact, w->h_kact, sizeof(int) * w->R, cudaMemcpyHostToDevice, st));
     if (w->mode == ARN_DF)
         arn_xupdate_df<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, x, ldx);
+    else if (w->mode == ARN_F32)
+        arn_xupdate_f32<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, x, ldx);
     else
         arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
     ARNC(cudaGetLastError());

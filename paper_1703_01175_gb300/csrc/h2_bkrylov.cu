@@ -29,7 +29,7 @@ static h2_status bk_true_residual(h2_handle *h, ArnWork *w, const double2 *b, in
     const int n = h->n, R = w->R;
     h2_status s;
     if (refine) {
-        const h2_prec acc = w->mode == ARN_DF ? H2_PREC_DFACC : H2_PREC_FP64ACC;
+        const h2_prec acc = w->mode != ARN_FP64 ? H2_PREC_DFACC : H2_PREC_FP64ACC;
         for (int r = 0; r < R; ++r)
             if ((s = h2_matvec(h, x + (size_t)r * ldx, w->tmp + (size_t)r * n, 1, n, acc, st)) != H2_OK)
                 return s;

@@ -101,7 +101,7 @@ void set_error(const std::string &msg);
 
 // FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
 struct ArnDev {
-    double2 *V;        // basis [(m+1)][R][n] (float4 hi/lo pairs in double-float mode)
+    double2 *V;        // basis [(m+1)][R][n] (float4 hi/lo pairs in double-float mode, float2 in FP32 mode)
     double2 *w;        // [R][n] vector being orthogonalised (likewise)
     double2 *part;     // [R][np] partial sums of the reductions
     unsigned *ticket;  // [R][8] last-block counters
@@ -112,7 +112,8 @@ struct ArnDev {
     int n, m, R, np;
 };
 
-enum { ARN_FP64 = 0, ARN_DF = 1 };  // Arnoldi arithmetic: FP64, or double-float on the FP32 pipes
+// Arnoldi arithmetic: FP64; double-float on the FP32 pipes; c64 basis with FP32 products
+enum { ARN_FP64 = 0, ARN_DF = 1, ARN_F32 = 2 };
 
 struct ArnWork {
     ArnDev K{};

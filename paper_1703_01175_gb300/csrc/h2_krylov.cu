@@ -34,7 +34,7 @@ static h2_status true_residual(h2_handle *h, ArnWork *w, const double2 *b, const
     if (x_zero) return arn_residual(w, b, n, nullptr, st);
     h2_status s;
     if (refine) {
-        const h2_prec acc = w->mode == ARN_DF ? H2_PREC_DFACC : H2_PREC_FP64ACC;
+        const h2_prec acc = w->mode != ARN_FP64 ? H2_PREC_DFACC : H2_PREC_FP64ACC;
         if ((s = h2_matvec(h, x, w->tmp, 1, n, acc, st)) != H2_OK) return s;
     } else {
         if ((s = arn_c128_to_c64(w, x, n, w->x32, st)) != H2_OK) return s;

@@ -50,7 +50,7 @@ class _Stats(ctypes.Structure):
 
 
 # arithmetic of the Gram-Schmidt passes: FP64, or double-float on the FP32 pipes
-ARNOLDI = {"fp64": 0, "df": 1}
+ARNOLDI = {"fp64": 0, "df": 1, "fp32": 2}
 
 
 class _SolveOpts(ctypes.Structure):

@@ -102,7 +102,22 @@ def test_gmres_double_float_arnoldi(mats, refine):
     assert np.linalg.norm(x2 - xo) <= 50 * tol * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("arnoldi", ["fp64", "df"])
+@pytest.mark.parametrize("tol", [1e-4, 1e-6])
+def test_gmres_fp32_basis_arnoldi(mats, tol):
+    """c64 basis with FP32 products and compensated sums: converges to the
+    tolerance against the oracle's FP64 residual, in about the iterations of
+    the FP64 Arnoldi (ragged case: 630 unknowns, row segments with tails)."""
+    c = cases.get("ragged")
+    b = synth.random_complex(c.n, 19)
+    bt = torch.from_numpy(b).cuda()
+    x1, i1 = mats["ragged"].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True)
+    x2, i2 = mats["ragged"].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True, arnoldi="fp32", reorth_eta=0.1)
+    assert i2[0]["status"] == 0, i2
+    assert _oracle_res(c, x2.cpu().numpy(), b) <= tol * 1.05
+    assert i2[0]["iterations"] <= i1[0]["iterations"] * 1.1 + 3, (i1, i2)
+
+
+@pytest.mark.parametrize("arnoldi", ["fp64", "df", "fp32"])
 @pytest.mark.parametrize("prec", ["splitbf16", "fp32"])
 def test_batched_gmres_matches_oracle(mats, prec, arnoldi):
     """Batched GMRES (one multi-RHS product per Arnoldi step): every column's

@@ -561,9 +561,33 @@ __global__ void __launch_bounds__(AT) arn_dot_f32(ArnDev K, int j, int S, int se
     reduce_columns(part, ncols, S, (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2));
 }
 
-// w -= V h with a c64 basis: four basis columns per group (plain FMAs, four
-// loads in flight), groups added compensated; |w'|^2 in FP64. Dynamic shared
-// memory: m + 2 float2 entries.
+// w -= V h with a c64 basis: each thread owns two rows (i, i + AT) and sweeps
+// the basis four columns at a time (eight loads in flight, h shared by both
+// rows), plain FMAs within a group, groups added compensated; |w'|^2 in FP64.
+// Dynamic shared memory: m + 2 float2 entries.
+__device__ __forceinline__ void f32_group(float &sr, float &cr, float &si, float &ci, float2 va, float2 vb, float2 vc,
+                                          float2 vd, float2 ha, float2 hb, float2 hc, float2 hd)
+{
+    float tr = va.y * ha.y;   // -Re(v h), four columns
+    tr = fmaf(-va.x, ha.x, tr);
+    tr = fmaf(-vb.x, hb.x, tr);
+    tr = fmaf(vb.y, hb.y, tr);
+    tr = fmaf(-vc.x, hc.x, tr);
+    tr = fmaf(vc.y, hc.y, tr);
+    tr = fmaf(-vd.x, hd.x, tr);
+    tr = fmaf(vd.y, hd.y, tr);
+    float ti = -va.x * ha.y;  // -Im(v h)
+    ti = fmaf(-va.y, ha.x, ti);
+    ti = fmaf(-vb.x, hb.y, ti);
+    ti = fmaf(-vb.y, hb.x, ti);
+    ti = fmaf(-vc.x, hc.y, ti);
+    ti = fmaf(-vc.y, hc.x, ti);
+    ti = fmaf(-vd.x, hd.y, ti);
+    ti = fmaf(-vd.y, hd.x, ti);
+    csum(sr, cr, tr);
+    csum(si, ci, ti);
+}
+
 template <bool SECOND>
 __global__ void __launch_bounds__(AT) arn_update_f32(ArnDev K, int j, int rows)
 {
@@ -578,42 +602,38 @@ __global__ void __launch_bounds__(AT) arn_update_f32(ArnDev K, int j, int rows)
     const float2 *V = reinterpret_cast<const float2 *>(K.V) + (size_t)r * K.n;
     const size_t ldv = (size_t)K.R * K.n;
     double nrm = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += AT) {
-        const float2 w0 = w[i];
-        float sr = w0.x, cr = 0.f, si = w0.y, ci = 0.f;
+    for (int i = i0 + threadIdx.x; i < i1; i += 2 * AT) {
+        const bool two = i + AT < i1;
+        const int k = two ? i + AT : i;   // without a second row, row i twice (result dropped)
+        const float2 w0 = w[i], w1 = w[k];
+        float sr0 = w0.x, cr0 = 0.f, si0 = w0.y, ci0 = 0.f;
+        float sr1 = w1.x, cr1 = 0.f, si1 = w1.y, ci1 = 0.f;
         int l = 0;
         for (; l + 3 <= j; l += 4) {
-            const float2 va = ldcs2(V + (size_t)l * ldv + i), vb = ldcs2(V + (size_t)(l + 1) * ldv + i);
-            const float2 vc = ldcs2(V + (size_t)(l + 2) * ldv + i), vd = ldcs2(V + (size_t)(l + 3) * ldv + i);
+            const float2 *c0 = V + (size_t)l * ldv, *c1 = c0 + ldv, *c2 = c1 + ldv, *c3 = c2 + ldv;
+            const float2 a0 = ldcs2(c0 + i), b0 = ldcs2(c1 + i), e0 = ldcs2(c2 + i), d0 = ldcs2(c3 + i);
+            const float2 a1 = ldcs2(c0 + k), b1 = ldcs2(c1 + k), e1 = ldcs2(c2 + k), d1 = ldcs2(c3 + k);
             const float2 ha = hs32[l], hb = hs32[l + 1], hc = hs32[l + 2], hd = hs32[l + 3];
-            float tr = va.y * ha.y;   // -Re(v h), four columns
-            tr = fmaf(-va.x, ha.x, tr);
-            tr = fmaf(-vb.x, hb.x, tr);
-            tr = fmaf(vb.y, hb.y, tr);
-            tr = fmaf(-vc.x, hc.x, tr);
-            tr = fmaf(vc.y, hc.y, tr);
-            tr = fmaf(-vd.x, hd.x, tr);
-            tr = fmaf(vd.y, hd.y, tr);
-            float ti = -va.x * ha.y;  // -Im(v h)
-            ti = fmaf(-va.y, ha.x, ti);
-            ti = fmaf(-vb.x, hb.y, ti);
-            ti = fmaf(-vb.y, hb.x, ti);
-            ti = fmaf(-vc.x, hc.y, ti);
-            ti = fmaf(-vc.y, hc.x, ti);
-            ti = fmaf(-vd.x, hd.y, ti);
-            ti = fmaf(-vd.y, hd.x, ti);
-            csum(sr, cr, tr);
-            csum(si, ci, ti);
+            f32_group(sr0, cr0, si0, ci0, a0, b0, e0, d0, ha, hb, hc, hd);
+            f32_group(sr1, cr1, si1, ci1, a1, b1, e1, d1, ha, hb, hc, hd);
         }
         for (; l <= j; ++l) {
-            const float2 v = ldcs2(V + (size_t)l * ldv + i), hh = hs32[l];
-            csum(sr, cr, fmaf(v.y, hh.y, -v.x * hh.x));
-            csum(si, ci, fmaf(-v.y, hh.x, -v.x * hh.y));
+            const float2 v0 = ldcs2(V + (size_t)l * ldv + i), v1 = ldcs2(V + (size_t)l * ldv + k), hh = hs32[l];
+            csum(sr0, cr0, fmaf(v0.y, hh.y, -v0.x * hh.x));
+            csum(si0, ci0, fmaf(-v0.y, hh.x, -v0.x * hh.y));
+            csum(sr1, cr1, fmaf(v1.y, hh.y, -v1.x * hh.x));
+            csum(si1, ci1, fmaf(-v1.y, hh.x, -v1.x * hh.y));
         }
-        const float2 o = make_float2(__fadd_rn(sr, cr), __fadd_rn(si, ci));
-        w[i] = o;
-        nrm = fma((double)o.x, (double)o.x, nrm);
-        nrm = fma((double)o.y, (double)o.y, nrm);
+        const float2 o0 = make_float2(__fadd_rn(sr0, cr0), __fadd_rn(si0, ci0));
+        w[i] = o0;
+        nrm = fma((double)o0.x, (double)o0.x, nrm);
+        nrm = fma((double)o0.y, (double)o0.y, nrm);
+        if (two) {
+            const float2 o1 = make_float2(__fadd_rn(sr1, cr1), __fadd_rn(si1, ci1));
+            w[k] = o1;
+            nrm = fma((double)o1.x, (double)o1.x, nrm);
+            nrm = fma((double)o1.y, (double)o1.y, nrm);
+        }
     }
     const double2 tot = block_sum(make_double2(nrm, 0.0));
     double2 *part = K.part + (size_t)r * K.np;
@@ -633,37 +653,40 @@ __global__ void __launch_bounds__(AT) arn_update_f32(ArnDev K, int j, int rows)
     K.scal[8 * r] = sqrt(nw2);
 }
 
-// v_{jn} = w / beta (c64); x32 = the same vector
-__global__ void arn_normalize_f32(ArnDev K, int jn, float2 *__restrict__ x32)
+// v_{jn} = w / beta (c64), four entries per thread in flight; the product of
+// the next step reads v_{jn} in place
+__global__ void arn_normalize_f32(ArnDev K, int jn)
 {
     const int r = blockIdx.y;
     const double beta = K.scal[8 * r];
-    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    const float inv = (float)(beta > 0.0 ? 1.0 / beta : 0.0);
     float2 *Vn = reinterpret_cast<float2 *>(K.V) + ((size_t)jn * K.R + r) * K.n;
     const float2 *w = reinterpret_cast<const float2 *>(K.w) + (size_t)r * K.n;
-    float2 *x = x32 + (size_t)r * K.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
-        const float2 v = w[i];
-        const float2 q = make_float2((float)(v.x * inv), (float)(v.y * inv));
-        Vn[i] = q;
-        x[i] = q;
+    const int stride = gridDim.x * blockDim.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < K.n; i += 4 * stride) {
+        const float2 a = w[i], b = w[i + stride], c = w[i + 2 * stride], d = w[i + 3 * stride];
+        Vn[i] = make_float2(a.x * inv, a.y * inv);
+        Vn[i + stride] = make_float2(b.x * inv, b.y * inv);
+        Vn[i + 2 * stride] = make_float2(c.x * inv, c.y * inv);
+        Vn[i + 3 * stride] = make_float2(d.x * inv, d.y * inv);
+    }
+    for (; i < K.n; i += stride) {
+        const float2 a = w[i];
+        Vn[i] = make_float2(a.x * inv, a.y * inv);
     }
 }
 
-// v_0 = rr / beta (c64); x32 = the same vector
-__global__ void arn_start_f32(ArnDev K, const double2 *__restrict__ rr, float2 *__restrict__ x32)
+// v_0 = rr / beta (c64), read in place by the first product
+__global__ void arn_start_f32(ArnDev K, const double2 *__restrict__ rr)
 {
     const int r = blockIdx.y;
     const double beta = K.scal[8 * r];
     const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
     float2 *V0 = reinterpret_cast<float2 *>(K.V) + (size_t)r * K.n;
     const double2 *v = rr + (size_t)r * K.n;
-    float2 *x = x32 + (size_t)r * K.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
-        const float2 q = make_float2((float)(v[i].x * inv), (float)(v[i].y * inv));
-        V0[i] = q;
-        x[i] = q;
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x)
+        V0[i] = make_float2((float)(v[i].x * inv), (float)(v[i].y * inv));
 }
 
 // x += V y (c128 x, c64 basis, FP64 FMAs: once per restart cycle)
@@ -841,7 +864,7 @@ h2_status arn_start(ArnWork *w, cudaStream_t st)
     if (w->mode == ARN_DF)
         arn_start_df<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
     else if (w->mode == ARN_F32)
-        arn_start_f32<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
+        arn_start_f32<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr);
     else
         arn_start<<<vec_grid(w), 256, 0, st>>>(w->K, w->rr, w->x32);
     ARNC(cudaGetLastError());
@@ -926,7 +949,7 @@ h2_status arn_step(ArnWork *w, int j, cudaStream_t st)
         arn_update_f32<false><<<gu, AT, smem, st>>>(K, j, w->rows);
         arn_dot_f32<true><<<g2, AT, 0, st>>>(K, j, S, seg);
         arn_update_f32<true><<<gu, AT, smem, st>>>(K, j, w->rows);
-        arn_normalize_f32<<<vec_grid(w), 256, 0, st>>>(K, j + 1, w->x32);
+        arn_normalize_f32<<<vec_grid(w), 256, 0, st>>>(K, j + 1);
     } else {
         arn_widen<<<vec_grid(w), 256, 0, st>>>(K, w->y32);
         arn_dot<false><<<g1, AT, 0, st>>>(K, j, S, seg);
@@ -941,6 +964,12 @@ h2_status arn_step(ArnWork *w, int j, cudaStream_t st)
     ARNC(cudaStreamSynchronize(st));
     for (int r = 0; r < w->R; ++r) host_column(w, r, j);
     return H2_OK;
+}
+
+const float2 *arn_input(const ArnWork *w, int j)
+{
+    if (w->mode == ARN_F32) return reinterpret_cast<const float2 *>(w->K.V) + (size_t)j * w->R * w->n;
+    return w->x32;
 }
 
 h2_status arn_read(ArnWork *w, cudaStream_t st)

@@ -98,7 +98,7 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
         std::fill(conv.begin(), conv.end(), -1);
         int k = 0;
         for (int j = 0; j < m && it < opts->maxit; ++j) {
-            if ((s = h2_matvec(h, w->x32, w->y32, R, n, prec, st)) != H2_OK) return s;
+            if ((s = h2_matvec(h, arn_input(w, j), w->y32, R, n, prec, st)) != H2_OK) return s;
             if ((s = arn_step(w, j, st)) != H2_OK) return s;
             ++it;
             k = j + 1;

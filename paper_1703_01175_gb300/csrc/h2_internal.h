@@ -139,9 +139,11 @@ h2_status arn_set_eta(ArnWork *w, double eta);
 void arn_free(ArnWork *w);
 // rr = b - y (y NULL: rr = b); scal[8 r] = |rr_r|
 h2_status arn_residual(ArnWork *w, const double2 *b, int64_t ldb, const double2 *y, cudaStream_t st);
-// v_0 = rr / |rr|, x32 = c64(v_0), g = |rr| e_1 (|rr| from h_scal: call arn_read first)
+// v_0 = rr / |rr| (and x32 = c64(v_0) unless FP32 mode), g = |rr| e_1 (|rr| from h_scal: call arn_read first)
 h2_status arn_start(ArnWork *w, cudaStream_t st);
-// with y32 = A x32: orthogonalise, v_{j+1} and x32 = c64(v_{j+1}); then (host)
+// input of the product of step j: v_j in c64, [R][n] (x32, or the basis column itself in FP32 mode)
+const float2 *arn_input(const ArnWork *w, int j);
+// with y32 = A arn_input(j): orthogonalise, v_{j+1} (and x32 = c64(v_{j+1}) unless FP32 mode); then (host)
 // Hessenberg column j, rotations, est / beta / bad / reorth per right-hand side
 h2_status arn_step(ArnWork *w, int j, cudaStream_t st);
 // copy scal to h_scal and synchronise

@@ -94,7 +94,7 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
             if (pc && (s = h2_apply_precond(h, w->K.V, w->Z, w->x32, st)) != H2_OK) return s;
             int k = 0;
             for (int j = 0; j < m && it < opts->maxit; ++j) {
-                if ((s = h2_matvec(h, w->x32, w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
+                if ((s = h2_matvec(h, pc ? w->x32 : arn_input(w, j), w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
                 if ((s = arn_step(w, j, st)) != H2_OK) return s;
                 ++it;
                 k = j + 1;

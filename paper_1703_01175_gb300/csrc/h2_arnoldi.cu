@@ -561,9 +561,10 @@ __global__ void __launch_bounds__(AT) arn_dot_f32(ArnDev K, int j, int S, int se
     reduce_columns(part, ncols, S, (SECOND ? K.h2 : K.h1) + (size_t)r * (K.m + 2));
 }
 
-// w -= V h with a c64 basis: each thread owns two rows (i, i + AT) and sweeps
-// the basis four columns at a time (eight loads in flight, h shared by both
-// rows), plain FMAs within a group, groups added compensated; |w'|^2 in FP64.
+// w -= V h with a c64 basis: each thread owns two rows (adjacent ones as one
+// float4 when n is even, else i and i + AT) and sweeps the basis four columns
+// at a time (h shared by both rows), plain FMAs within a group, groups added
+// compensated; |w'|^2 in FP64.
 // Dynamic shared memory: m + 2 float2 entries.
 __device__ __forceinline__ void f32_group(float &sr, float &cr, float &si, float &ci, float2 va, float2 vb, float2 vc,
                                           float2 vd, float2 ha, float2 hb, float2 hc, float2 hd)
@@ -602,6 +603,44 @@ __global__ void __launch_bounds__(AT) arn_update_f32(ArnDev K, int j, int rows)
     const float2 *V = reinterpret_cast<const float2 *>(K.V) + (size_t)r * K.n;
     const size_t ldv = (size_t)K.R * K.n;
     double nrm = 0.0;
+    if ((K.n & 1) == 0) {
+        // even n: every column starts on 16 bytes and row blocks on even rows, so
+        // a thread takes rows 2p, 2p + 1 as one float4 (512 contiguous bytes per
+        // column per warp)
+        const float4 *V4 = reinterpret_cast<const float4 *>(V);
+        const size_t ldv4 = ldv / 2;
+        float4 *w4 = reinterpret_cast<float4 *>(w);
+        for (int q = i0 / 2 + threadIdx.x; q < i1 / 2; q += AT) {
+            const float4 w0 = w4[q];
+            float sr0 = w0.x, cr0 = 0.f, si0 = w0.y, ci0 = 0.f;
+            float sr1 = w0.z, cr1 = 0.f, si1 = w0.w, ci1 = 0.f;
+            int l = 0;
+            for (; l + 3 <= j; l += 4) {
+                const float4 *c0 = V4 + (size_t)l * ldv4 + q;
+                const float4 a = ldcs4(c0), b = ldcs4(c0 + ldv4), e = ldcs4(c0 + 2 * ldv4), d = ldcs4(c0 + 3 * ldv4);
+                const float2 ha = hs32[l], hb = hs32[l + 1], hc = hs32[l + 2], hd = hs32[l + 3];
+                f32_group(sr0, cr0, si0, ci0, make_float2(a.x, a.y), make_float2(b.x, b.y), make_float2(e.x, e.y),
+                          make_float2(d.x, d.y), ha, hb, hc, hd);
+                f32_group(sr1, cr1, si1, ci1, make_float2(a.z, a.w), make_float2(b.z, b.w), make_float2(e.z, e.w),
+                          make_float2(d.z, d.w), ha, hb, hc, hd);
+            }
+            for (; l <= j; ++l) {
+                const float4 v = ldcs4(V4 + (size_t)l * ldv4 + q);
+                const float2 hh = hs32[l];
+                csum(sr0, cr0, fmaf(v.y, hh.y, -v.x * hh.x));
+                csum(si0, ci0, fmaf(-v.y, hh.x, -v.x * hh.y));
+                csum(sr1, cr1, fmaf(v.w, hh.y, -v.z * hh.x));
+                csum(si1, ci1, fmaf(-v.w, hh.x, -v.z * hh.y));
+            }
+            const float4 o = make_float4(__fadd_rn(sr0, cr0), __fadd_rn(si0, ci0), __fadd_rn(sr1, cr1),
+                                         __fadd_rn(si1, ci1));
+            w4[q] = o;
+            nrm = fma((double)o.x, (double)o.x, nrm);
+            nrm = fma((double)o.y, (double)o.y, nrm);
+            nrm = fma((double)o.z, (double)o.z, nrm);
+            nrm = fma((double)o.w, (double)o.w, nrm);
+        }
+    } else
     for (int i = i0 + threadIdx.x; i < i1; i += 2 * AT) {
         const bool two = i + AT < i1;
         const int k = two ? i + AT : i;   // without a second row, row i twice (result dropped)

@@ -65,6 +65,9 @@ def get(name: str) -> Case:
     if name == "ragged":
         v = synth.random_eps_grid((7, 5, 6), (1 / 16,) * 3, 2.0, 6.0, seed=3)
         return Case(name, v, 40, 1e-4)
+    if name == "odd":  # 175 voxels: an odd number of unknowns (525)
+        v = synth.random_eps_grid((7, 5, 5), (1 / 16,) * 3, 2.0, 6.0, seed=9)
+        return Case(name, v, 40, 1e-4)
     if name == "cube12":
         v = synth.random_eps_grid((12, 12, 12), (1 / 16,) * 3, 2.0, 6.0, seed=12)
         return Case(name, v, 96, 1e-4)

@@ -22,7 +22,7 @@ def mats():
     from paper_1703_01175_gb300 import build, h2
     build.build_all()
     out = {}
-    for name in ("cube8", "cube12", "ragged"):
+    for name in ("cube8", "cube12", "ragged", "odd"):
         out[name] = h2.H2Matrix(cases.get(name).arrays())
     yield out
     for m in out.values():
@@ -102,19 +102,35 @@ def test_gmres_double_float_arnoldi(mats, refine):
     assert np.linalg.norm(x2 - xo) <= 50 * tol * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("tol", [1e-4, 1e-6])
-def test_gmres_fp32_basis_arnoldi(mats, tol):
+@pytest.mark.parametrize("name,tol", [("ragged", 1e-4), ("ragged", 1e-6), ("odd", 1e-5)])
+def test_gmres_fp32_basis_arnoldi(mats, name, tol):
     """c64 basis with FP32 products and compensated sums: converges to the
     tolerance against the oracle's FP64 residual, in about the iterations of
-    the FP64 Arnoldi (ragged case: 630 unknowns, row segments with tails)."""
-    c = cases.get("ragged")
+    the FP64 Arnoldi (ragged: 630 unknowns, row segments with tails; odd: 525
+    unknowns, the update pass's two-strided-rows path)."""
+    c = cases.get(name)
     b = synth.random_complex(c.n, 19)
     bt = torch.from_numpy(b).cuda()
-    x1, i1 = mats["ragged"].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True)
-    x2, i2 = mats["ragged"].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True, arnoldi="fp32", reorth_eta=0.1)
+    x1, i1 = mats[name].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True)
+    x2, i2 = mats[name].gmres(bt, tol=tol, restart=40, maxit=2000, refine=True, arnoldi="fp32", reorth_eta=0.1)
     assert i2[0]["status"] == 0, i2
     assert _oracle_res(c, x2.cpu().numpy(), b) <= tol * 1.05
     assert i2[0]["iterations"] <= i1[0]["iterations"] * 1.1 + 3, (i1, i2)
+
+
+def test_batched_gmres_fp32_basis_odd_n(mats):
+    """Batched solve with the c64 basis on an odd number of unknowns: every
+    column's oracle FP64 residual within the tolerance."""
+    c = cases.get("odd")
+    R = 3
+    B = np.asfortranarray(synth.random_complex(c.n, 29, cols=R))
+    Bt = torch.from_numpy(B).cuda().t().contiguous().t()
+    X, info = mats["odd"].gmres_batched(Bt, tol=1e-4, restart=30, maxit=2000, refine=True, prec="splitbf16",
+                                        arnoldi="fp32", reorth_eta=0.1)
+    X = X.cpu().numpy()
+    for j in range(R):
+        assert info[j]["status"] == 0, info[j]
+        assert _oracle_res(c, X[:, j], B[:, j]) <= 1.05e-4
 
 
 @pytest.mark.parametrize("arnoldi", ["fp64", "df", "fp32"])

@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-CASES = ["cube8", "ragged", "cube12", "slab", "array", "single_leaf", "tiny_leaves"]
+CASES = ["cube8", "ragged", "cube12", "slab", "array", "single_leaf", "tiny_leaves", "odd"]
 
 
 @pytest.fixture(scope="module")
@@ -133,7 +133,7 @@ def test_multi_rhs_fp32_matches_oracle(loaded, name, R):
 
 @pytest.mark.parametrize("pipeline", [True, False])
 @pytest.mark.parametrize("name,R", [("cube12", 128), ("cube12", 5), ("ragged", 130), ("slab", 64),
-                                    ("array", 17), ("tiny_leaves", 3)])
+                                    ("array", 17), ("tiny_leaves", 3), ("odd", 7)])
 def test_splitbf16_tensor_cores_match_oracle(loaded, name, R, pipeline):
     """Split-bf16 tcgen05 path (deepest pipeline and two stages): within
     eps = 1e-4 of the oracle's FP64 product

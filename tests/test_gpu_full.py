@@ -4,7 +4,8 @@ the H^2 data of the host constructor, the launch configuration bench.py times.
 - FP32 product vs the oracle's FP64 H^2 product on the same data: 1e-5;
 - sampled rows against the oracle's dense VIE rows, evaluated one by one:
   representation error within 10 eps;
-- GMRES to 1e-4 (single right-hand side, and the batched double-float solve):
+- GMRES to 1e-4 (single right-hand side, and the batched solve with the c64
+  and the double-float basis):
   the oracle's FP64 residual of each GPU solution <= 1.05e-4. This
   random-permittivity cube is hard for restarted GMRES: with m = 50 the
   residual stagnates near 7e-4 (the GPU and the oracle agree on that on the
@@ -90,15 +91,18 @@ def test_full_size_accumulated_products_agree(full):
     assert float(torch.linalg.norm(ya - yd) / torch.linalg.norm(ya)) <= 1e-12
 
 
-def test_full_size_batched_double_float_gmres(full):
-    """The batched solve bench.py times (split-bf16 products, double-float
-    Arnoldi and restart residuals, m = 400) on 4 plane waves: the oracle's
-    FP64 residual of every solution <= 1.05 tol."""
+@pytest.mark.parametrize("arnoldi", ["fp32", "df"])
+def test_full_size_batched_gmres(full, arnoldi):
+    """The batched solve bench.py times (split-bf16 products, c64-basis
+    Arnoldi with eta = 0.1, double-float restart residuals, m = 400; and the
+    double-float-basis variant) on 4 plane waves: the oracle's FP64 residual
+    of every solution <= 1.05 tol."""
     w, arrs, perm, A, hZ = full
     R = 4
     B = synth.random_plane_waves(w.voxels, R, seed=5)[(3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)]
     Bt = torch.from_numpy(np.asfortranarray(B)).cuda().t().contiguous().t()
-    X, info = A.gmres_batched(Bt, tol=w.tol, restart=400, maxit=3000, refine=True, prec="splitbf16", arnoldi="df")
+    X, info = A.gmres_batched(Bt, tol=w.tol, restart=400, maxit=3000, refine=True, prec="splitbf16", arnoldi=arnoldi,
+                              reorth_eta=0.1)
     X = X.cpu().numpy()
     for j in range(R):
         assert info[j]["status"] == 0, info[j]

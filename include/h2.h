@@ -120,7 +120,16 @@ typedef struct {
  * default 2^24; when one runs out the kernel waits for its copies and MMAs in
  * flight, skips its output, frees its tensor memory and flags the handle, so
  * that h2_device_status returns H2_ERR_TIMEOUT; 0 makes every first wait run
- * out, which tests that path).
+ * out, which tests that path), "sym_couple=0|1" (default 0; 1: the single-RHS
+ * FP32 product keeps each coupling once per admissible pair, S^{t,s} with
+ * s > t in cluster order, and reads it once for both S^{t,s} xh^s and
+ * (S^{t,s})^T xh^t, since S^{s,t} = (S^{t,s})^T for the one-basis form of
+ * the complex-symmetric kernel (Eq. 8); the transposed contributions go
+ * through a scratch vector summed in a fixed order, so the product stays
+ * deterministic. Built on the first such product, on the device, from the
+ * loaded couplings: H2_ERR_STATE when some |S^{s,t} - (S^{t,s})^T| exceeds
+ * 1e-5 of max |S^{t,s}| or a rank exceeds 128. Every other product path keeps
+ * the full storage).
  */
 h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);
@@ -195,6 +204,16 @@ typedef struct {
 } h2_stats;
 
 h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
+
+/*
+ * Symmetric coupling storage of a handle loaded with "sym_couple=1" (built
+ * here if no product has built it yet): complex entries of the stored blocks
+ * (about half of coupling_elems), scratch entries (one per stored column) and
+ * the largest relative difference max |S^{s,t} - (S^{t,s})^T| / max |S^{t,s}|
+ * over the pairs. H2_ERR_STATE for a handle without the option or with
+ * non-symmetric couplings.
+ */
+h2_status h2_sym_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_entries, double *max_asym);
 
 /*
  * Time the stages of a single-RHS FP32 product with CUDA events recorded on

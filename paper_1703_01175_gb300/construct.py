@@ -584,6 +584,14 @@ def build_vie_h2(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI,
     for t, s in adm:  # zero-rank couplings
         if (t, s) not in S:
             S[(t, s)] = np.zeros((int(rank[t]), int(rank[s])), dtype=np.complex128)
+    # K is complex symmetric and both sides use the same basis, so Eq. 18 gives
+    # S^{s,t} = (S^{t,s})^T; the two skeleton estimates above agree only to the
+    # truncation accuracy, and their mean restores the symmetry exactly
+    for t, s in adm:
+        if t < s:
+            m = 0.5 * (S[(t, s)] + S[(s, t)].T)
+            S[(t, s)] = m
+            S[(s, t)] = m.T.copy()
     secs["couplings"] = time.time() - t0
     if verbose:
         print(f"construct: couplings {secs['couplings']:.1f} s", flush=True)

@@ -233,6 +233,7 @@ void h2_free(h2_handle *h)
     cudaDeviceSynchronize();
     h2_free_krylov(h);
     h2_free_split(h);
+    h2::h2_free_sym(h);
     h2_free_precond(h);
     h2_free_bkrylov(h);
     h2_free_bicgstab(h);
@@ -356,7 +357,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     if (st != H2_OK) return st;
 
     int device = 0;
-    bool use_graphs = true, tc_pipeline = true;
+    bool use_graphs = true, tc_pipeline = true, sym_couple = false;
     uint32_t wait_limit = 1u << 24;
     if (opts) {
         const char *p = strstr(opts, "device=");
@@ -365,6 +366,8 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         if (g) use_graphs = atoi(g + 7) != 0;
         const char *tp = strstr(opts, "tc_pipeline=");
         if (tp) tc_pipeline = atoi(tp + 12) != 0;
+        const char *sc = strstr(opts, "sym_couple=");
+        if (sc) sym_couple = atoi(sc + 11) != 0;
         const char *wl = strstr(opts, "wait_limit=");
         if (wl) {
             const long long v = atoll(wl + 11);
@@ -378,6 +381,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     h->use_graphs = use_graphs;
     h->tc_pipeline = tc_pipeline;
     h->wait_limit = wait_limit;
+    h->sym_couple = sym_couple;
     const int32_t n = tree->n, nc = tree->n_clusters, nl = tree->n_levels;
     h->n = n;
     h->nc = nc;
@@ -719,7 +723,7 @@ h2_status h2_load_file(const char *path, const char *opts, h2_handle **out)
     if (!path || !out) return arg_error("h2_load_file: NULL argument");
     *out = nullptr;
     int device = 0;
-    bool use_graphs = true, tc_pipeline = true;
+    bool use_graphs = true, tc_pipeline = true, sym_couple = false;
     uint32_t wait_limit = 1u << 24;
     if (opts) {
         const char *p = strstr(opts, "device=");
@@ -728,6 +732,8 @@ h2_status h2_load_file(const char *path, const char *opts, h2_handle **out)
         if (g) use_graphs = atoi(g + 7) != 0;
         const char *tp = strstr(opts, "tc_pipeline=");
         if (tp) tc_pipeline = atoi(tp + 12) != 0;
+        const char *sc = strstr(opts, "sym_couple=");
+        if (sc) sym_couple = atoi(sc + 11) != 0;
         const char *wl = strstr(opts, "wait_limit=");
         if (wl) {
             const long long v = atoll(wl + 11);
@@ -764,6 +770,7 @@ h2_status h2_load_file(const char *path, const char *opts, h2_handle **out)
     h->use_graphs = use_graphs;
     h->tc_pipeline = tc_pipeline;
     h->wait_limit = wait_limit;
+    h->sym_couple = sym_couple;
     h->n = n;
     h->nc = nc;
     h->nlev = nl;
@@ -829,6 +836,21 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out)
     return H2_OK;
 }
 
+h2_status h2_sym_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_entries, double *max_asym)
+{
+    if (!h || !stored_elems || !scratch_entries || !max_asym) return arg_error("h2_sym_stats: NULL argument");
+    if (!h->sym_couple) return (set_error("h2_sym_stats: the handle was loaded without sym_couple=1"), H2_ERR_STATE);
+    H2_CUDA(cudaSetDevice(h->device));
+    if (!h->sym) {
+        const h2_status s = h2::h2_sym_init(h);
+        if (s != H2_OK) return s;
+    }
+    *stored_elems = h->sym->stored_elems;
+    *scratch_entries = h->sym->scratch_entries;
+    *max_asym = h->sym->max_asym;
+    return H2_OK;
+}
+
 }  // extern "C"
 
 // ---- products -------------------------------------------------------------------------
@@ -854,7 +876,12 @@ static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st, b
     H2_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
     H2_CUDA(launch(h->upleaf, x, coef, 0, st));
     for (int l = h->nlev - 1; l >= 0; --l) H2_CUDA(launch(h->up[l], x, coef, 0, st));
-    H2_CUDA(launch(h->couple, x, coef, 0, st));
+    if constexpr (std::is_same<VT, float2>::value) {
+        if (h->sym) H2_CUDA(h2::h2_sym_couple(h, coef, st));   // couplings stored once per pair
+        else H2_CUDA(launch(h->couple, x, coef, 0, st));
+    } else {
+        H2_CUDA(launch(h->couple, x, coef, 0, st));
+    }
     for (int l = 0; l < h->nlev; ++l) H2_CUDA(launch(h->down[l], x, coef, 1, st));
     H2_CUDA(cudaStreamWaitEvent(st, h->ev_near, 0));
     H2_CUDA(launch(h->leafexp, x, y, 1, st));
@@ -925,6 +952,10 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
                                   reinterpret_cast<float2 *>(y), nrhs > 1 ? ld : h->n, nrhs, st);
     if (nrhs > 1 && prec == H2_PREC_FP32)
         return h2_run_multi_f32(h, reinterpret_cast<const float2 *>(x), ld, reinterpret_cast<float2 *>(y), ld, nrhs, st);
+    if (nrhs == 1 && prec == H2_PREC_FP32 && h->sym_couple && !h->sym) {
+        const h2_status s = h2::h2_sym_init(h);   // before any graph capture
+        if (s != H2_OK) return s;
+    }
     if (nrhs == 1 && prec == H2_PREC_FP32 && h->use_graphs)
         return run_single_graph(h, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), st);
     for (int32_t r = 0; r < nrhs; ++r) {
@@ -975,6 +1006,10 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
 {
     if (!h || !x || !y || !ms || iters < 1 || n_ms < 1) return arg_error("h2_profile_matvec: bad argument");
     H2_CUDA(cudaSetDevice(h->device));
+    if (h->sym_couple && !h->sym) {
+        const h2_status s = h2::h2_sym_init(h);
+        if (s != H2_OK) return s;
+    }
     cudaStream_t st = h->s_aux;
     const float2 *xx = reinterpret_cast<const float2 *>(x);
     float2 *yy = reinterpret_cast<float2 *>(y);
@@ -992,7 +1027,8 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
         for (int l = h->nlev - 1; l >= 0; --l)
             H2_CUDA(launch_phase_f32(h->up[l], h->d_mat, h->d_segs, xx, coef, coef, 0, st));
         H2_CUDA(cudaEventRecord(ev[3], st));
-        H2_CUDA(launch_phase_f32(h->couple, h->d_mat, h->d_segs, xx, coef, coef, 0, st));
+        if (h->sym) H2_CUDA(h2::h2_sym_couple(h, coef, st));
+        else H2_CUDA(launch_phase_f32(h->couple, h->d_mat, h->d_segs, xx, coef, coef, 0, st));
         H2_CUDA(cudaEventRecord(ev[4], st));
         for (int l = 0; l < h->nlev; ++l)
             H2_CUDA(launch_phase_f32(h->down[l], h->d_mat, h->d_segs, xx, coef, coef, 1, st));

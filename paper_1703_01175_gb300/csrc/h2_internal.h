@@ -99,6 +99,25 @@ struct SplitState {
 
 void set_error(const std::string &msg);
 
+// Couplings stored once per admissible pair (h2_sym.cu): tasks hold the blocks
+// S^{t,s} with s > t; scratch holds (S^{t,s})^T xh^t, one entry per stored
+// column; gather lists add those into yh^s.
+struct SymState {
+    int ntask = 0, ntarget = 0;
+    Task *d_tasks = nullptr;
+    Seg *d_segs = nullptr;
+    float2 *d_mat = nullptr;
+    int64_t *d_col0 = nullptr;     // per task: first scratch entry
+    float2 *d_scratch = nullptr;
+    int32_t *d_gptr = nullptr;     // per target cluster: range of gcol [ntarget + 1]
+    int64_t *d_gcol = nullptr;     // scratch entry of column 0 of each (t, s), t < s
+    int32_t *d_gout = nullptr;     // offset of yh^s in the coefficient buffer
+    int32_t *d_gk = nullptr;       // rank of s
+    int64_t stored_elems = 0;      // complex entries of the stored blocks
+    int64_t scratch_entries = 0;
+    float max_asym = 0.f;          // largest |S^{t,s} - (S^{s,t})^T| / max |S^{t,s}| over the pairs
+};
+
 // FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
 struct ArnDev {
     double2 *V;        // basis [(m+1)][R][n] (float4 hi/lo pairs in double-float mode, float2 in FP32 mode)
@@ -203,6 +222,8 @@ struct h2_handle {
     uint32_t wait_limit = 1u << 24;   // polls of the tensor-core kernels' bounded waits
     cudaStream_t s_cap = nullptr;
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
+    bool sym_couple = false;          // single-RHS FP32 product: couplings stored once per pair
+    h2::SymState *sym = nullptr;      // built on first use (h2_sym.cu)
 };
 
 void h2_free_krylov(h2_handle *h);
@@ -210,6 +231,11 @@ h2_status h2_ensure_coefm(h2_handle *h, int nrhs);
 // column index tables of every phase for the multi-RHS kernels (built once)
 h2_status h2_ensure_colidx(h2_handle *h);
 void h2_free_split(h2_handle *h);
+namespace h2 {
+h2_status h2_sym_init(h2_handle *h);
+void h2_free_sym(h2_handle *h);
+cudaError_t h2_sym_couple(h2_handle *h, float2 *coef, cudaStream_t st);
+}  // namespace h2
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st);
 h2_status h2_split_error_flag(h2_handle *h, int *flag);

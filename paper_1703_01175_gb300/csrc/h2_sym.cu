@@ -1,0 +1,475 @@
+// Symmetric storage of the couplings for the single-RHS FP32 product.
+//
+// The couplings come from the H^2 form of the complex-symmetric kernel with
+// one basis per cluster (Eq. 8), so S^{s,t} = (S^{t,s})^T for every admissible
+// pair. This path keeps only the blocks with s > t (cluster index) and makes
+// one pass over them:
+//
+//   direct      yh^t += S^{t,s} xh^s          (the task's own output)
+//   transposed  c_{s<-t} = (S^{t,s})^T xh^t   (one entry per stored column)
+//
+// so every stored entry is read from HBM once and serves both products. The
+// transposed contributions go to a scratch vector (one entry per stored
+// column); a second launch adds, for every cluster s, the contributions of all
+// t < s in a fixed order. No atomics: the product stays deterministic.
+//
+// Thread mapping of the dual kernel: a warp covers CS = 32 / Pp columns at a
+// time, Pp lanes per column (Pp = the power of two >= the task's row pairs P,
+// between 8 and 32; tasks with 32 < P <= 64 give every lane a second row
+// pair).
+// Lane rl holds rows 2 rl, 2 rl + 1 (and + 64) of a column as one 16-byte
+// load; the direct sums stay in registers, the transposed sum of a column is
+// a shuffle reduction over its Pp lanes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <unordered_map>
+#include <vector>
+
+#include "h2_internal.h"
+
+namespace h2 {
+namespace {
+
+constexpr int SYM_THREADS = 256;
+constexpr int SYM_WARPS = SYM_THREADS / 32;
+constexpr int SYM_CHUNK = 4096;   // staged input columns per pass (32 KB)
+constexpr int SYM_UNROLL = 4;     // columns in flight per slot
+
+__device__ __forceinline__ void cmac_pair(float &ar, float &ai, float &br, float &bi, float4 m, float2 x)
+{
+    ar = fmaf(m.x, x.x, ar);
+    ar = fmaf(-m.y, x.y, ar);
+    ai = fmaf(m.x, x.y, ai);
+    ai = fmaf(m.y, x.x, ai);
+    br = fmaf(m.z, x.x, br);
+    br = fmaf(-m.w, x.y, br);
+    bi = fmaf(m.z, x.y, bi);
+    bi = fmaf(m.w, x.x, bi);
+}
+
+// (S^{t,s})^T xh^t restricted to this lane's rows: sum of m[row] * xt[row]
+__device__ __forceinline__ void tdot(float &tr, float &ti, float4 m, float2 u, float2 v)
+{
+    tr = fmaf(m.x, u.x, tr);
+    tr = fmaf(-m.y, u.y, tr);
+    ti = fmaf(m.x, u.y, ti);
+    ti = fmaf(m.y, u.x, ti);
+    tr = fmaf(m.z, v.x, tr);
+    tr = fmaf(-m.w, v.y, tr);
+    ti = fmaf(m.z, v.y, ti);
+    ti = fmaf(m.w, v.x, ti);
+}
+
+// Reduce v[0..7] (Re, Im of four columns) over the Pp lanes of a column slot
+// (8 <= Pp <= 32, a power of two): three halving steps leave each lane one of
+// the eight partial sums (index 4 b16 + 2 b8 + b4 from its lane bits
+// Pp/2, Pp/4, Pp/8), the remaining steps add across the rest of the slot;
+// 9 shuffles for Pp = 32 instead of 40 separate reductions.
+__device__ __forceinline__ float slot_reduce8(float v[8], int Pp, int rl, int &idx)
+{
+    int o = Pp >> 1;
+    idx = 0;
+#pragma unroll
+    for (int h = 4; h >= 1; h >>= 1) {   // halving steps: 8 -> 4 -> 2 -> 1 values
+        const bool up = (rl & o) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = up ? v[k] : v[k + h];
+            const float keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        idx += up ? h : 0;
+        o >>= 1;
+    }
+    float r = v[0];
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+template <bool TWO>
+__device__ __forceinline__ void symcouple_task(const Task &tk, int64_t col0, const Seg *__restrict__ segs,
+                                               const float2 *__restrict__ mat, float2 *coef, int64_t ktot,
+                                               float2 *__restrict__ scratch, float2 *xs)
+{
+    const int P = tk.mpad >> 1;   // 1 <= P <= 32 (TWO: 32 < P <= 64)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int Pp = 8;
+    while (Pp < P && Pp < 32) Pp <<= 1;
+    const int CS = 32 / Pp;
+    const int sl = lane / Pp, rl = lane % Pp;
+    const bool has0 = rl < P, has1 = TWO && rl + 32 < P;
+    const int slot = warp * CS + sl, nslot = SYM_WARPS * CS;
+
+    // own coefficients xh^t (rows of the task) for the transposed products
+    const float2 *xt = coef + (tk.out_off - ktot);
+    const float2 z2 = make_float2(0.f, 0.f);
+    const float2 u0 = has0 && 2 * rl < tk.m ? xt[2 * rl] : z2;
+    const float2 v0 = has0 && 2 * rl + 1 < tk.m ? xt[2 * rl + 1] : z2;
+    const float2 u1 = has1 && 2 * rl + 64 < tk.m ? xt[2 * rl + 64] : z2;
+    const float2 v1 = has1 && 2 * rl + 65 < tk.m ? xt[2 * rl + 65] : z2;
+
+    float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f, b0r = 0.f, b0i = 0.f, b1r = 0.f, b1i = 0.f;
+    const float4 *A = reinterpret_cast<const float4 *>(mat + tk.mat_off);
+    float *sc = reinterpret_cast<float *>(scratch + col0);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (int c0 = 0; c0 < tk.ncol; c0 += SYM_CHUNK) {
+        const int cn = min(SYM_CHUNK, tk.ncol - c0);
+        __syncthreads();
+        int cpos = 0;
+        for (int s = tk.seg_begin; s < tk.seg_end && cpos < c0 + cn; ++s) {
+            const Seg sg = segs[s];
+            const int lo = max(cpos, c0), hi = min(cpos + sg.n, c0 + cn);
+            if (lo < hi) {
+                const float2 *src = coef + (-(int64_t)sg.in_off - 1);   // xh^s
+                for (int c = lo + threadIdx.x; c < hi; c += SYM_THREADS) xs[c - c0] = src[c - cpos];
+            }
+            cpos += sg.n;
+        }
+        __syncthreads();
+        // batches of SYM_UNROLL columns per slot; every lane of a warp runs the
+        // same trip count (the shuffles need the whole warp); the next batch's
+        // loads are issued before this batch is reduced
+        const int nb = (cn + nslot * SYM_UNROLL - 1) / (nslot * SYM_UNROLL);
+        float4 m0[SYM_UNROLL], m1[SYM_UNROLL];
+        auto load = [&](int bi) {
+#pragma unroll
+            for (int q = 0; q < SYM_UNROLL; ++q) {
+                const int c = slot + (bi * SYM_UNROLL + q) * nslot;
+                const bool ok = bi < nb && c < cn;
+                const float4 *Ac = A + (size_t)(c0 + c) * P;
+                m0[q] = ok && has0 ? __ldcs(Ac + rl) : z4;
+                if (TWO) m1[q] = ok && has1 ? __ldcs(Ac + rl + 32) : z4;
+            }
+        };
+        load(0);
+        for (int bi = 0; bi < nb; ++bi) {
+            float4 n0[SYM_UNROLL], n1[SYM_UNROLL];
+#pragma unroll
+            for (int q = 0; q < SYM_UNROLL; ++q) {
+                n0[q] = m0[q];
+                if (TWO) n1[q] = m1[q];
+            }
+            load(bi + 1);
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < SYM_UNROLL; ++q) {
+                const int c = slot + (bi * SYM_UNROLL + q) * nslot;
+                const float2 x = c < cn ? xs[c] : z2;
+                float tr = 0.f, ti = 0.f;
+                cmac_pair(a0r, a0i, a1r, a1i, n0[q], x);
+                tdot(tr, ti, n0[q], u0, v0);
+                if (TWO) {
+                    cmac_pair(b0r, b0i, b1r, b1i, n1[q], x);
+                    tdot(tr, ti, n1[q], u1, v1);
+                }
+                v[2 * q] = tr;
+                v[2 * q + 1] = ti;
+            }
+            int idx;
+            const float r = slot_reduce8(v, Pp, rl, idx);
+            // every lane holds the full sum of value idx (column idx / 2, Re or Im);
+            // the lanes whose bits below Pp / 8 are zero write the eight of them
+            const int c = slot + (bi * SYM_UNROLL + (idx >> 1)) * nslot;
+            if ((rl & ((Pp >> 3) - 1)) == 0 && c < cn) sc[2 * (c0 + c) + (idx & 1)] = r;
+        }
+    }
+    // direct sums: one partial per (slot, row), summed over the slots in a fixed order
+    __syncthreads();
+    float2 *red = xs;   // nslot * mpad <= 1024 entries
+    if (has0) {
+        red[slot * tk.mpad + 2 * rl] = make_float2(a0r, a0i);
+        red[slot * tk.mpad + 2 * rl + 1] = make_float2(a1r, a1i);
+    }
+    if (has1) {
+        red[slot * tk.mpad + 2 * rl + 64] = make_float2(b0r, b0i);
+        red[slot * tk.mpad + 2 * rl + 65] = make_float2(b1r, b1i);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < tk.m; i += SYM_THREADS) {
+        float sr = 0.f, si = 0.f;
+        for (int s = 0; s < nslot; ++s) {
+            const float2 v = red[s * tk.mpad + i];
+            sr += v.x;
+            si += v.y;
+        }
+        coef[tk.out_off + i] = make_float2(sr, si);
+    }
+}
+
+// one block per task (tasks sorted by stored work, both row-pair layouts in
+// one launch so that small tasks fill in behind large ones)
+__global__ void __launch_bounds__(SYM_THREADS, 3)
+symcouple_kernel(const Task *__restrict__ tasks, const Seg *__restrict__ segs, const float2 *__restrict__ mat,
+                 const int64_t *__restrict__ col0, float2 *coef, int64_t ktot, float2 *__restrict__ scratch)
+{
+    __shared__ __align__(16) float2 xs[SYM_CHUNK];
+    const Task tk = tasks[blockIdx.x];
+    if (tk.mpad > 64)
+        symcouple_task<true>(tk, col0[blockIdx.x], segs, mat, coef, ktot, scratch, xs);
+    else
+        symcouple_task<false>(tk, col0[blockIdx.x], segs, mat, coef, ktot, scratch, xs);
+}
+
+// yh^s += sum over t < s of c_{s<-t}, in a fixed order (one block per cluster s)
+__global__ void symgather_kernel(const int32_t *__restrict__ gptr, const int64_t *__restrict__ gcol,
+                                 const int32_t *__restrict__ gout, const int32_t *__restrict__ gk,
+                                 const float2 *__restrict__ scratch, float2 *__restrict__ coef)
+{
+    const int tg = blockIdx.x;
+    const int k = gk[tg], e0 = gptr[tg], e1 = gptr[tg + 1];
+    float2 *o = coef + gout[tg];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        float sr = o[i].x, si = o[i].y;
+        for (int e = e0; e < e1; ++e) {
+            const float2 v = scratch[gcol[e] + i];
+            sr += v.x;
+            si += v.y;
+        }
+        o[i] = make_float2(sr, si);
+    }
+}
+
+// copy the kept columns into the symmetric matrix: one block per task
+__global__ void symcopy_kernel(const Task *__restrict__ tasks, const int64_t *__restrict__ col0,
+                               const int64_t *__restrict__ colsrc, const float2 *__restrict__ src,
+                               float2 *__restrict__ dst)
+{
+    const Task tk = tasks[blockIdx.x];
+    const int64_t base = col0[blockIdx.x];
+    const int64_t total = (int64_t)tk.ncol * tk.mpad;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int64_t j = e / tk.mpad, i = e - j * tk.mpad;
+        dst[tk.mat_off + e] = src[colsrc[base + j] + i];
+    }
+}
+
+// per stored block: max |S^{t,s} - (S^{s,t})^T| / max |S^{t,s}|, maximum over
+// blocks in *worst (non-negative floats order like their bit patterns)
+struct SymPair {
+    int64_t a, b;      // offsets of S^{t,s} (rows k_t, stride mpa) and S^{s,t} (rows k_s, stride mpb)
+    int32_t mpa, mpb, kt, ks;
+};
+
+__global__ void symcheck_kernel(const SymPair *__restrict__ pairs, const float2 *__restrict__ mat,
+                                unsigned *__restrict__ worst)
+{
+    const SymPair p = pairs[blockIdx.x];
+    float d = 0.f, g = 0.f;
+    for (int e = threadIdx.x; e < p.kt * p.ks; e += blockDim.x) {
+        const int j = e / p.kt, i = e - j * p.kt;   // row i of t, column j of s
+        const float2 a = mat[p.a + (int64_t)j * p.mpa + i];
+        const float2 b = mat[p.b + (int64_t)i * p.mpb + j];
+        d = fmaxf(d, hypotf(a.x - b.x, a.y - b.y));
+        g = fmaxf(g, hypotf(a.x, a.y));
+    }
+    __shared__ float sd[256], sg[256];
+    sd[threadIdx.x] = d;
+    sg[threadIdx.x] = g;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sd[threadIdx.x] = fmaxf(sd[threadIdx.x], sd[threadIdx.x + o]);
+            sg[threadIdx.x] = fmaxf(sg[threadIdx.x], sg[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const float r = sd[0] > 0.f ? sd[0] / fmaxf(sg[0], 1e-30f) : 0.f;
+        atomicMax(worst, __float_as_uint(r));
+    }
+}
+
+}  // namespace
+
+#define SY_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t e__ = (call);                                                     \
+        if (e__ != cudaSuccess) {                                                     \
+            cudaGetLastError();                                                       \
+            set_error(std::string("symmetric couplings: ") + #call + ": " + cudaGetErrorString(e__)); \
+            return e__ == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA;    \
+        }                                                                             \
+    } while (0)
+
+void h2_free_sym(h2_handle *h)
+{
+    SymState *S = h->sym;
+    if (!S) return;
+    for (void *p : {(void *)S->d_tasks, (void *)S->d_segs, (void *)S->d_mat, (void *)S->d_col0,
+                    (void *)S->d_scratch, (void *)S->d_gptr, (void *)S->d_gcol, (void *)S->d_gout, (void *)S->d_gk})
+        cudaFree(p);
+    delete S;
+    h->sym = nullptr;
+}
+
+// Build the symmetric coupling data from the handle's coupling tasks (device
+// copy of the kept columns) and check S^{s,t} = (S^{t,s})^T on the device.
+h2_status h2_sym_init(h2_handle *h)
+{
+    if (h->sym) return H2_OK;
+    const Phase &C = h->couple;
+    const std::vector<Seg> &hsegs = h->segs_host;
+    std::unordered_map<int32_t, int32_t> cluster_of_xo;
+    for (int t = 0; t < h->nc; ++t)
+        if (h->rank[t] > 0) cluster_of_xo[h->xo[t]] = t;
+    struct Blk {
+        int64_t off;
+        int32_t mpad, kt, ks;
+    };
+    std::unordered_map<int64_t, Blk> blocks;   // key t * nc + s
+    for (const Task &tk : C.tasks) {
+        const auto it = cluster_of_xo.find((int32_t)(tk.out_off - h->ktot));
+        if (it == cluster_of_xo.end()) return (set_error("symmetric couplings: unknown output cluster"), H2_ERR_STATE);
+        const int32_t t = it->second;
+        int col = 0;
+        for (int si = tk.seg_begin; si < tk.seg_end; ++si) {
+            const Seg &sg = hsegs[si];
+            const auto is = sg.in_off < 0 ? cluster_of_xo.find((int32_t)(-(int64_t)sg.in_off - 1)) : cluster_of_xo.end();
+            if (is == cluster_of_xo.end() || h->rank[is->second] != sg.n)
+                return (set_error("symmetric couplings: a coupling input is not a cluster's coefficient block"), H2_ERR_STATE);
+            blocks[(int64_t)t * h->nc + is->second] = {tk.mat_off + (int64_t)col * tk.mpad, tk.mpad, tk.m, sg.n};
+            col += sg.n;
+        }
+    }
+    // kept blocks (s > t) per task, in the handle's task order
+    std::vector<Task> tasks;
+    std::vector<Seg> segs;
+    std::vector<int64_t> col0, colsrc;
+    std::vector<SymPair> pairs;
+    std::vector<std::vector<int64_t>> lower(h->nc);   // per cluster s: first scratch column of each (t, s), t < s
+    int64_t mat_elems = 0, ncols = 0, stored = 0;
+    for (const Task &tk : C.tasks) {
+        if (tk.mpad > 128) return (set_error("symmetric couplings: ranks above 128 are not supported"), H2_ERR_STATE);
+        const int32_t t = cluster_of_xo.at((int32_t)(tk.out_off - h->ktot));
+        Task u = tk;
+        u.ncol = 0;
+        u.mat_off = mat_elems;
+        u.seg_begin = (int32_t)segs.size();
+        const int64_t c0 = ncols;
+        for (int si = tk.seg_begin; si < tk.seg_end; ++si) {
+            const Seg &sg = hsegs[si];
+            const int32_t s = cluster_of_xo.at((int32_t)(-(int64_t)sg.in_off - 1));
+            if (s <= t) continue;
+            const auto back = blocks.find((int64_t)s * h->nc + t);
+            if (back == blocks.end())
+                return (set_error("symmetric couplings: admissible pair without its transpose"), H2_ERR_STATE);
+            const Blk &f = blocks.at((int64_t)t * h->nc + s);
+            for (int j = 0; j < sg.n; ++j) colsrc.push_back(f.off + (int64_t)j * f.mpad);
+            lower[s].push_back(c0 + u.ncol);
+            pairs.push_back({f.off, back->second.off, f.mpad, back->second.mpad, f.kt, f.ks});
+            segs.push_back(sg);
+            u.ncol += sg.n;
+            stored += (int64_t)f.kt * f.ks;
+        }
+        u.seg_end = (int32_t)segs.size();
+        if (u.ncol == 0) continue;
+        tasks.push_back(u);
+        col0.push_back(c0);
+        ncols += u.ncol;
+        mat_elems += ((int64_t)u.mpad * u.ncol + 31) / 32 * 32;
+    }
+    // largest stored work first
+    {
+        std::vector<size_t> ord(tasks.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t i, size_t j) {
+            return (int64_t)tasks[i].mpad * tasks[i].ncol > (int64_t)tasks[j].mpad * tasks[j].ncol;
+        });
+        std::vector<Task> t2;
+        std::vector<int64_t> c2;
+        for (size_t i : ord) {
+            t2.push_back(tasks[i]);
+            c2.push_back(col0[i]);
+        }
+        tasks.swap(t2);
+        col0.swap(c2);
+    }
+    std::vector<int32_t> gptr(1, 0), gout, gk;
+    std::vector<int64_t> gcol;
+    for (int s = 0; s < h->nc; ++s) {
+        if (lower[s].empty()) continue;
+        gcol.insert(gcol.end(), lower[s].begin(), lower[s].end());
+        gptr.push_back((int32_t)gcol.size());
+        gout.push_back((int32_t)(h->ktot + h->xo[s]));
+        gk.push_back(h->rank[s]);
+    }
+
+    auto *S = new SymState();
+    h->sym = S;
+    S->ntask = (int)tasks.size();
+    S->ntarget = (int)gout.size();
+    S->stored_elems = stored;
+    S->scratch_entries = ncols;
+    auto fail = [&](h2_status st) {
+        h2_free_sym(h);
+        return st;
+    };
+    auto up = [&](auto &vec, auto **dptr) -> cudaError_t {
+        using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+        cudaError_t e = cudaMalloc(dptr, std::max<size_t>(1, vec.size()) * sizeof(T));
+        if (e == cudaSuccess && !vec.empty()) e = cudaMemcpy(*dptr, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice);
+        return e;
+    };
+    int64_t *d_colsrc = nullptr;
+    SymPair *d_pairs = nullptr;
+    unsigned *d_worst = nullptr;
+    auto tmp_free = [&]() {
+        cudaFree(d_colsrc);
+        cudaFree(d_pairs);
+        cudaFree(d_worst);
+    };
+    cudaError_t e = cudaSuccess;
+    if ((e = up(tasks, &S->d_tasks)) != cudaSuccess || (e = up(segs, &S->d_segs)) != cudaSuccess ||
+        (e = up(col0, &S->d_col0)) != cudaSuccess || (e = up(gptr, &S->d_gptr)) != cudaSuccess ||
+        (e = up(gcol, &S->d_gcol)) != cudaSuccess || (e = up(gout, &S->d_gout)) != cudaSuccess ||
+        (e = up(gk, &S->d_gk)) != cudaSuccess || (e = up(colsrc, &d_colsrc)) != cudaSuccess ||
+        (e = up(pairs, &d_pairs)) != cudaSuccess ||
+        (e = cudaMalloc(&S->d_mat, std::max<int64_t>(32, mat_elems) * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&S->d_scratch, std::max<int64_t>(1, ncols) * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&d_worst, sizeof(unsigned))) != cudaSuccess || (e = cudaMemset(d_worst, 0, sizeof(unsigned))) != cudaSuccess) {
+        cudaGetLastError();
+        tmp_free();
+        set_error(std::string("symmetric couplings: device allocation failed: ") + cudaGetErrorString(e));
+        return fail(e == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA);
+    }
+    if (S->ntask > 0) symcopy_kernel<<<S->ntask, 256>>>(S->d_tasks, S->d_col0, d_colsrc, h->d_mat, S->d_mat);
+    if (!pairs.empty()) symcheck_kernel<<<(unsigned)pairs.size(), 256>>>(d_pairs, h->d_mat, d_worst);
+    unsigned worst = 0;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(&worst, d_worst, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    tmp_free();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("symmetric couplings: ") + cudaGetErrorString(e));
+        return fail(H2_ERR_CUDA);
+    }
+    float w;
+    memcpy(&w, &worst, sizeof(w));
+    S->max_asym = w;
+    if (!(w <= 1e-5f)) {
+        set_error("symmetric couplings: S^{s,t} differs from (S^{t,s})^T by " + std::to_string(w) +
+                  " relative (limit 1e-5)");
+        return fail(H2_ERR_STATE);
+    }
+    return H2_OK;
+}
+
+// couplings of all levels with the symmetric storage: yh = S xh (FP32)
+cudaError_t h2_sym_couple(h2_handle *h, float2 *coef, cudaStream_t st)
+{
+    const SymState *S = h->sym;
+    if (S->ntask > 0)
+        symcouple_kernel<<<S->ntask, SYM_THREADS, 0, st>>>(S->d_tasks, S->d_segs, S->d_mat, S->d_col0, coef, h->ktot,
+                                                           S->d_scratch);
+    if (S->ntarget > 0)
+        symgather_kernel<<<S->ntarget, 128, 0, st>>>(S->d_gptr, S->d_gcol, S->d_gout, S->d_gk, S->d_scratch, coef);
+    return cudaGetLastError();
+}
+
+}  // namespace h2

@@ -94,6 +94,9 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_int64, ctypes.c_int]
     L.h2_get_stats.restype = ctypes.c_int
     L.h2_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Stats)]
+    L.h2_sym_stats.restype = ctypes.c_int
+    L.h2_sym_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_double)]
     L.h2_profile_matvec.restype = ctypes.c_int
     L.h2_profile_matvec.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int32]
@@ -131,7 +134,7 @@ def _check(status: int, where: str):
 
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
-    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats",
+    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats",
             "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_autotune",
             "h2_status_string", "h2_last_error"]
 
@@ -223,7 +226,7 @@ class H2Matrix:
     """A loaded H^2 operator on one GPU (wraps an h2_handle)."""
 
     def __init__(self, arrs: H2Arrays, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,
-                 wait_limit: int | None = None):
+                 wait_limit: int | None = None, sym_couple: bool = False):
         L = lib()
         cplx = arrs.U.dtype
         if cplx not in (np.complex64, np.complex128):
@@ -248,7 +251,7 @@ class H2Matrix:
                   _ip(arrs.near_ptr, _i32p), _ip(arrs.near_col, _i32p),
                   arrs.Z.ctypes.data, _ip(arrs.Z_off, _i64p), arrs.Z.size)
         h = ctypes.c_void_p()
-        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)}"
+        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)};sym_couple={int(sym_couple)}"
         if wait_limit is not None:
             opts += f";wait_limit={int(wait_limit)}"
         _check(L.h2_load(ctypes.byref(tr), ctypes.byref(d), opts.encode(), ctypes.byref(h)), "h2_load")
@@ -258,9 +261,9 @@ class H2Matrix:
 
     @classmethod
     def from_file(cls, path: str, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,
-                  wait_limit: int | None = None) -> "H2Matrix":
+                  wait_limit: int | None = None, sym_couple: bool = False) -> "H2Matrix":
         """Reload an operator written by save() (no re-validation or re-packing)."""
-        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)}"
+        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)};sym_couple={int(sym_couple)}"
         if wait_limit is not None:
             opts += f";wait_limit={int(wait_limit)}"
         h = ctypes.c_void_p()
@@ -295,6 +298,12 @@ class H2Matrix:
         s = _Stats()
         _check(lib().h2_get_stats(self._h, ctypes.byref(s)), "h2_get_stats")
         return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def sym_stats(self) -> dict:
+        """Symmetric coupling storage (handle loaded with sym_couple=True)."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().h2_sym_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "h2_sym_stats")
+        return {"stored_elems": a.value, "scratch_entries": b.value, "max_asym": c.value}
 
     def matvec(self, x, y=None, prec: str = "fp32", stream=None):
         """y = A x on the device. x: torch complex64 (fp32, splitbf16) or

@@ -11,7 +11,8 @@ the H^2 data of the host constructor, the launch configuration bench.py times.
   residual stagnates near 7e-4 (the GPU and the oracle agree on that on the
   smaller 16^3 version), so the solves use m = 400;
 - split-bf16 products of 8 right-hand sides: sampled columns within eps;
-- double-float and FP64 accumulation agree to 1e-12.
+- double-float and FP64 accumulation agree to 1e-12;
+- couplings stored once per admissible pair: within 1e-6 of full storage.
 """
 import math
 
@@ -108,3 +109,27 @@ def test_full_size_batched_gmres(full, arnoldi):
         assert info[j]["status"] == 0, info[j]
         res = np.linalg.norm(B[:, j] - h2mv.h2_matvec(hZ, X[:, j])) / np.linalg.norm(B[:, j])
         assert res <= 1.05 * w.tol
+
+
+def test_full_size_symmetric_couplings(full):
+    """Couplings stored once per admissible pair at full size (ranks up to 79,
+    so tasks with a second row pair per lane run too): exactly half the
+    coupling entries stored, exact symmetry of the constructed couplings, and
+    the product within 1e-6 of the full-storage product and within 1e-5 of the
+    oracle's FP64 product on the same data."""
+    from paper_1703_01175_gb300 import h2
+    w, arrs, perm, A, hZ = full
+    B = h2.H2Matrix(arrs, sym_couple=True)
+    try:
+        st = B.sym_stats()
+        assert 2 * st["stored_elems"] == A.stats()["coupling_elems"]
+        assert st["max_asym"] == 0.0
+        x = synth.random_complex(arrs.n, 25)
+        xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+        ys = B.matvec(xt).cpu().numpy()
+        yf = A.matvec(xt).cpu().numpy()
+        assert np.linalg.norm(ys - yf) <= 1e-6 * np.linalg.norm(yf)
+        yo = h2mv.h2_matvec(hZ, x.astype(np.complex64).astype(np.complex128))
+        assert np.linalg.norm(ys - yo) <= 1e-5 * np.linalg.norm(yo)
+    finally:
+        B.close()

@@ -237,3 +237,60 @@ def test_save_and_reload_reproduce_products(loaded, tmp_path):
     with pytest.raises(h2.H2Error) as e:
         h2.H2Matrix.from_file(str(bad))
     assert e.value.status == 1   # H2_ERR_ARG
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_symmetric_couplings_match_oracle(loaded, name):
+    """Couplings stored once per admissible pair (sym_couple): the product
+    matches the oracle within 1e-5 and the full-storage product within 1e-6,
+    replays bitwise (graph and direct launches), and stores exactly half of
+    the coupling entries."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get(name)
+    full = _mat(loaded, name)
+    A = h2.H2Matrix(c.arrays(), sym_couple=True)
+    B = h2.H2Matrix(c.arrays(), sym_couple=True, graphs=False)
+    try:
+        st = A.sym_stats()
+        assert 2 * st["stored_elems"] == full.stats()["coupling_elems"]
+        assert st["max_asym"] <= 1e-6
+        for seed in (3, 4):
+            x = synth.random_complex(c.n, seed)
+            xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+            y1 = A.matvec(xt).clone()
+            y2 = A.matvec(xt).clone()
+            y3 = B.matvec(xt)
+            assert torch.equal(y1, y2) and torch.equal(y1, y3)
+            y = y1.cpu().numpy()
+            assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+            assert _rel(y, full.matvec(xt).cpu().numpy()) <= 1e-6
+    finally:
+        A.close()
+        B.close()
+
+
+def test_symmetric_couplings_reject_asymmetric_data(loaded):
+    """A coupling block whose transpose partner differs is refused with
+    H2_ERR_STATE on the first product; the handle's full-storage paths and
+    other handles keep working."""
+    import dataclasses
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube8")
+    arrs = c.arrays()
+    S = arrs.S.copy()
+    j = int(np.argmax(np.diff(arrs.S_off)))            # a large block
+    S[arrs.S_off[j]] += 0.5 * np.abs(S).max()
+    bad = dataclasses.replace(arrs, S=S)
+    A = h2.H2Matrix(bad, sym_couple=True)
+    try:
+        x = torch.from_numpy(synth.random_complex(c.n, 5).astype(np.complex64)).cuda()
+        with pytest.raises(h2.H2Error) as e:
+            A.matvec(x)
+        assert e.value.status == 7   # H2_ERR_STATE
+        X = torch.from_numpy(np.asfortranarray(synth.random_complex(c.n, 6, cols=3).astype(np.complex64)))
+        A.matvec(X.cuda().t().contiguous().t(), prec="splitbf16")   # full storage still usable
+        assert A.device_status() == 0
+    finally:
+        A.close()
+    y = _mat(loaded, "cube8").matvec(x).cpu().numpy()
+    assert _rel(y, c.oracle_matvec(x.cpu().numpy().astype(np.complex128))) <= 1e-5

@@ -360,7 +360,7 @@ extern "C" h2_status h2_bicgstab(h2_handle *h, const void *b_, void *x_, int32_t
             }
             const bool breakdown = w->h_sc[S_FLAG].x != 0.0;
             if (rel <= opts->tol || breakdown) {
-                // judge by the true residual; restart from x when it is not small enough
+                // decide by the true residual; restart from x when it is not small enough
                 if (opts->refine || breakdown) {
                     if ((s = true_start(false)) != H2_OK) return s;
                     rel = std::sqrt(w->h_sc[S_RNORM2].x) / bnorm;

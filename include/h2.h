@@ -216,6 +216,27 @@ h2_status h2_get_stats(const h2_handle *h, h2_stats *out);
 h2_status h2_sym_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_entries, double *max_asym);
 
 /*
+ * Near field stored once per pair of leaves for the single-RHS FP32 product.
+ * The near blocks are Z^{t,s} = delta_ts I - K^{t,s} diag(chi_s) with K
+ * complex symmetric (Sec. II; chi = eps_r - 1 per unknown), so
+ *   Z^{s,t} = diag(1/chi_s) (Z^{t,s})^T diag(chi_t)   for t != s,
+ * and one stored block serves both directions: Z^{t,s} x_s directly and
+ * Z^{s,t} x_t = (1/chi_s) o (Z^{t,s})^T (chi_t o x_t), read once. chi: host
+ * array of n complex values (c64 or c128 by dtype) in tree order, copied.
+ * The structure is built here on the device from the loaded near blocks and
+ * every pair is checked against that relation (H2_ERR_STATE beyond 1e-5
+ * relative). H2_ERR_STATE as well when some chi is zero (a void voxel: its
+ * near-field columns are zero and do not determine their transposes) or a
+ * leaf has more than 128 unknowns. chi NULL returns to the full storage.
+ * Captured product graphs are dropped; other product paths are unaffected.
+ */
+h2_status h2_sym_near(h2_handle *h, const void *chi, h2_dtype dtype);
+/* Stored near-field entries (the diagonal blocks and one block per leaf
+   pair), scratch entries and the largest relative difference from the
+   relation above; H2_ERR_STATE when h2_sym_near has not been called. */
+h2_status h2_sym_near_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_entries, double *max_asym);
+
+/*
  * Time the stages of a single-RHS FP32 product with CUDA events recorded on
  * the stream each stage is launched on. x, y: device c64 vectors. Runs `iters`
  * products (after one warm-up) and writes the mean duration in milliseconds

@@ -872,7 +872,12 @@ static h2_status run_single(h2_handle *h, const VT *x, VT *y, cudaStream_t st, b
     H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(VT) * 2 * std::max<int64_t>(1, h->ktot), st));
     H2_CUDA(cudaEventRecord(h->ev_fork, st));
     H2_CUDA(cudaStreamWaitEvent(h->s_aux, h->ev_fork, 0));
-    H2_CUDA(launch(h->near, x, y, 0, h->s_aux));
+    if constexpr (std::is_same<VT, float2>::value) {
+        if (h->symnear) H2_CUDA(h2::symnear_run(h, x, y, h->s_aux));   // near blocks stored once per leaf pair
+        else H2_CUDA(launch(h->near, x, y, 0, h->s_aux));
+    } else {
+        H2_CUDA(launch(h->near, x, y, 0, h->s_aux));
+    }
     H2_CUDA(cudaEventRecord(h->ev_near, h->s_aux));
     H2_CUDA(launch(h->upleaf, x, coef, 0, st));
     for (int l = h->nlev - 1; l >= 0; --l) H2_CUDA(launch(h->up[l], x, coef, 0, st));
@@ -935,6 +940,50 @@ static void drop_graphs(h2_handle *h)
 }
 
 extern "C" {
+
+h2_status h2_sym_near(h2_handle *h, const void *chi, h2_dtype dtype)
+{
+    if (!h) return arg_error("h2_sym_near: NULL handle");
+    if (chi && dtype != H2_C64 && dtype != H2_C128) return arg_error("h2_sym_near: bad dtype");
+    H2_CUDA(cudaSetDevice(h->device));
+    H2_CUDA(cudaDeviceSynchronize());
+    drop_graphs(h);   // captured products use the previous near-field structure
+    if (!chi) {
+        h2::symnear_free(h);
+        return H2_OK;
+    }
+    std::vector<float2> c(h->n);
+    for (int32_t i = 0; i < h->n; ++i) {
+        double re, im;
+        if (dtype == H2_C128) {
+            re = static_cast<const double *>(chi)[2 * i];
+            im = static_cast<const double *>(chi)[2 * i + 1];
+        } else {
+            re = static_cast<const float *>(chi)[2 * i];
+            im = static_cast<const float *>(chi)[2 * i + 1];
+        }
+        if (!std::isfinite(re) || !std::isfinite(im)) return arg_error("h2_sym_near: non-finite chi");
+        c[i] = make_float2((float)re, (float)im);
+        if (c[i].x == 0.f && c[i].y == 0.f) {
+            h2::symnear_free(h);
+            set_error("h2_sym_near: chi is zero at unknown " + std::to_string(i) +
+                      " (a void voxel): its near-field columns do not determine their transposes");
+            return H2_ERR_STATE;
+        }
+    }
+    return h2::symnear_init(h, c);
+}
+
+h2_status h2_sym_near_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_entries, double *max_asym)
+{
+    if (!h || !stored_elems || !scratch_entries || !max_asym) return arg_error("h2_sym_near_stats: NULL argument");
+    if (!h->symnear) return (set_error("h2_sym_near_stats: no symmetric near field (call h2_sym_near)"), H2_ERR_STATE);
+    *stored_elems = h->symnear->stored_elems;
+    *scratch_entries = h->symnear->scratch_entries;
+    *max_asym = h->symnear->max_asym;
+    return H2_OK;
+}
+
 
 h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t ld, h2_prec prec,
                     void *stream)
@@ -1020,7 +1069,8 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
     for (int it = 0; it <= iters; ++it) {
         H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * 2 * std::max<int64_t>(1, h->ktot), st));
         H2_CUDA(cudaEventRecord(ev[0], st));
-        H2_CUDA(launch_phase_f32(h->near, h->d_mat, h->d_segs, xx, coef, yy, 0, st));
+        if (h->symnear) H2_CUDA(h2::symnear_run(h, xx, yy, st));
+        else H2_CUDA(launch_phase_f32(h->near, h->d_mat, h->d_segs, xx, coef, yy, 0, st));
         H2_CUDA(cudaEventRecord(ev[1], st));
         H2_CUDA(launch_phase_f32(h->upleaf, h->d_mat, h->d_segs, xx, coef, coef, 0, st));
         H2_CUDA(cudaEventRecord(ev[2], st));

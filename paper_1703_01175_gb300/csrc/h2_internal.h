@@ -115,7 +115,10 @@ struct SymState {
     int32_t *d_gk = nullptr;       // rank of s
     int64_t stored_elems = 0;      // complex entries of the stored blocks
     int64_t scratch_entries = 0;
-    float max_asym = 0.f;          // largest |S^{t,s} - (S^{s,t})^T| / max |S^{t,s}| over the pairs
+    float max_asym = 0.f;          // largest relative difference of a stored block from its partner's relation
+    float2 *d_chi = nullptr;       // near field: chi per unknown (tree order)
+    float2 *d_rs = nullptr;        // near field: 1 / chi
+    float2 *d_xs = nullptr;        // near field: chi x of the current product
 };
 
 // FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
@@ -224,6 +227,7 @@ struct h2_handle {
     h2::SplitState *split = nullptr;  // split-bf16 tensor-core state (h2_umma.cu)
     bool sym_couple = false;          // single-RHS FP32 product: couplings stored once per pair
     h2::SymState *sym = nullptr;      // built on first use (h2_sym.cu)
+    h2::SymState *symnear = nullptr;  // near field stored once per leaf pair (h2_sym_near)
 };
 
 void h2_free_krylov(h2_handle *h);
@@ -235,6 +239,9 @@ namespace h2 {
 h2_status h2_sym_init(h2_handle *h);
 void h2_free_sym(h2_handle *h);
 cudaError_t h2_sym_couple(h2_handle *h, float2 *coef, cudaStream_t st);
+h2_status symnear_init(h2_handle *h, const std::vector<float2> &chi);
+void symnear_free(h2_handle *h);
+cudaError_t symnear_run(h2_handle *h, const float2 *x, float2 *y, cudaStream_t st);
 }  // namespace h2
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st);

@@ -91,9 +91,13 @@ __device__ __forceinline__ float slot_reduce8(float v[8], int Pp, int rl, int &i
     return r;
 }
 
+// One task: segments with in_off >= 0 read xin, others the coefficients; xt
+// is the task's own-row vector of the transposed products; the direct sums go
+// to out[out_off ...].
 template <bool TWO>
 __device__ __forceinline__ void symcouple_task(const Task &tk, int64_t col0, const Seg *__restrict__ segs,
-                                               const float2 *__restrict__ mat, float2 *coef, int64_t ktot,
+                                               const float2 *__restrict__ mat, const float2 *coef,
+                                               const float2 *xin, const float2 *xt, float2 *out,
                                                float2 *__restrict__ scratch, float2 *xs)
 {
     const int P = tk.mpad >> 1;   // 1 <= P <= 32 (TWO: 32 < P <= 64)
@@ -105,8 +109,6 @@ __device__ __forceinline__ void symcouple_task(const Task &tk, int64_t col0, con
     const bool has0 = rl < P, has1 = TWO && rl + 32 < P;
     const int slot = warp * CS + sl, nslot = SYM_WARPS * CS;
 
-    // own coefficients xh^t (rows of the task) for the transposed products
-    const float2 *xt = coef + (tk.out_off - ktot);
     const float2 z2 = make_float2(0.f, 0.f);
     const float2 u0 = has0 && 2 * rl < tk.m ? xt[2 * rl] : z2;
     const float2 v0 = has0 && 2 * rl + 1 < tk.m ? xt[2 * rl + 1] : z2;
@@ -126,7 +128,7 @@ __device__ __forceinline__ void symcouple_task(const Task &tk, int64_t col0, con
             const Seg sg = segs[s];
             const int lo = max(cpos, c0), hi = min(cpos + sg.n, c0 + cn);
             if (lo < hi) {
-                const float2 *src = coef + (-(int64_t)sg.in_off - 1);   // xh^s
+                const float2 *src = sg.in_off >= 0 ? xin + sg.in_off : coef + (-(int64_t)sg.in_off - 1);
                 for (int c = lo + threadIdx.x; c < hi; c += SYM_THREADS) xs[c - c0] = src[c - cpos];
             }
             cpos += sg.n;
@@ -198,40 +200,62 @@ __device__ __forceinline__ void symcouple_task(const Task &tk, int64_t col0, con
             sr += v.x;
             si += v.y;
         }
-        coef[tk.out_off + i] = make_float2(sr, si);
+        out[tk.out_off + i] = make_float2(sr, si);
     }
 }
 
 // one block per task (tasks sorted by stored work, both row-pair layouts in
 // one launch so that small tasks fill in behind large ones)
+// (couplings: xt = coef + out_off - ktot, out = coef; near field: xt = chi x
+// + out_off, out = y)
 __global__ void __launch_bounds__(SYM_THREADS, 3)
 symcouple_kernel(const Task *__restrict__ tasks, const Seg *__restrict__ segs, const float2 *__restrict__ mat,
-                 const int64_t *__restrict__ col0, float2 *coef, int64_t ktot, float2 *__restrict__ scratch)
+                 const int64_t *__restrict__ col0, const float2 *coef, const float2 *xin, const float2 *xtv,
+                 int64_t xt_shift, float2 *out, float2 *__restrict__ scratch)
 {
     __shared__ __align__(16) float2 xs[SYM_CHUNK];
     const Task tk = tasks[blockIdx.x];
+    const float2 *xt = xtv + (tk.out_off + xt_shift);
     if (tk.mpad > 64)
-        symcouple_task<true>(tk, col0[blockIdx.x], segs, mat, coef, ktot, scratch, xs);
+        symcouple_task<true>(tk, col0[blockIdx.x], segs, mat, coef, xin, xt, out, scratch, xs);
     else
-        symcouple_task<false>(tk, col0[blockIdx.x], segs, mat, coef, ktot, scratch, xs);
+        symcouple_task<false>(tk, col0[blockIdx.x], segs, mat, coef, xin, xt, out, scratch, xs);
 }
 
-// yh^s += sum over t < s of c_{s<-t}, in a fixed order (one block per cluster s)
+// out_s += rs_s * (sum over t < s of c_{s<-t}), in a fixed order (one block
+// per target s; rs NULL: no scale, else one complex factor per output entry)
 __global__ void symgather_kernel(const int32_t *__restrict__ gptr, const int64_t *__restrict__ gcol,
                                  const int32_t *__restrict__ gout, const int32_t *__restrict__ gk,
-                                 const float2 *__restrict__ scratch, float2 *__restrict__ coef)
+                                 const float2 *__restrict__ scratch, const float2 *__restrict__ rs,
+                                 float2 *__restrict__ out)
 {
     const int tg = blockIdx.x;
     const int k = gk[tg], e0 = gptr[tg], e1 = gptr[tg + 1];
-    float2 *o = coef + gout[tg];
+    float2 *o = out + gout[tg];
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        float sr = o[i].x, si = o[i].y;
+        float sr = 0.f, si = 0.f;
         for (int e = e0; e < e1; ++e) {
             const float2 v = scratch[gcol[e] + i];
             sr += v.x;
             si += v.y;
         }
-        o[i] = make_float2(sr, si);
+        if (rs) {
+            const float2 f = rs[gout[tg] + i];
+            const float tr = sr * f.x - si * f.y;
+            si = sr * f.y + si * f.x;
+            sr = tr;
+        }
+        o[i] = make_float2(o[i].x + sr, o[i].y + si);
+    }
+}
+
+// xs = chi x (near field: the transposed products use the scaled input)
+__global__ void symscale_kernel(const float2 *__restrict__ chi, const float2 *__restrict__ x, float2 *__restrict__ xs,
+                                int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 c = chi[i], v = x[i];
+        xs[i] = make_float2(c.x * v.x - c.y * v.y, c.x * v.y + c.y * v.x);
     }
 }
 
@@ -254,17 +278,25 @@ __global__ void symcopy_kernel(const Task *__restrict__ tasks, const int64_t *__
 struct SymPair {
     int64_t a, b;      // offsets of S^{t,s} (rows k_t, stride mpa) and S^{s,t} (rows k_s, stride mpb)
     int32_t mpa, mpb, kt, ks;
+    int32_t ra, cs;    // near field: unknown index of row 0 of t and of column 0 of s
 };
 
+// chi NULL: B^{s,t} against (B^{t,s})^T; else against diag(1/chi_s) (B^{t,s})^T diag(chi_t)
 __global__ void symcheck_kernel(const SymPair *__restrict__ pairs, const float2 *__restrict__ mat,
-                                unsigned *__restrict__ worst)
+                                const float2 *__restrict__ chi, unsigned *__restrict__ worst)
 {
     const SymPair p = pairs[blockIdx.x];
     float d = 0.f, g = 0.f;
     for (int e = threadIdx.x; e < p.kt * p.ks; e += blockDim.x) {
         const int j = e / p.kt, i = e - j * p.kt;   // row i of t, column j of s
-        const float2 a = mat[p.a + (int64_t)j * p.mpa + i];
+        float2 a = mat[p.a + (int64_t)j * p.mpa + i];
         const float2 b = mat[p.b + (int64_t)i * p.mpb + j];
+        if (chi) {
+            const float2 ct = chi[p.ra + i], cs = chi[p.cs + j];
+            const float2 u = make_float2(a.x * ct.x - a.y * ct.y, a.x * ct.y + a.y * ct.x);
+            const float den = cs.x * cs.x + cs.y * cs.y;
+            a = make_float2((u.x * cs.x + u.y * cs.y) / den, (u.y * cs.x - u.x * cs.y) / den);
+        }
         d = fmaxf(d, hypotf(a.x - b.x, a.y - b.y));
         g = fmaxf(g, hypotf(a.x, a.y));
     }
@@ -297,56 +329,70 @@ __global__ void symcheck_kernel(const SymPair *__restrict__ pairs, const float2 
         }                                                                             \
     } while (0)
 
-void h2_free_sym(h2_handle *h)
+namespace {
+
+void free_state(SymState *S)
 {
-    SymState *S = h->sym;
     if (!S) return;
     for (void *p : {(void *)S->d_tasks, (void *)S->d_segs, (void *)S->d_mat, (void *)S->d_col0,
-                    (void *)S->d_scratch, (void *)S->d_gptr, (void *)S->d_gcol, (void *)S->d_gout, (void *)S->d_gk})
+                    (void *)S->d_scratch, (void *)S->d_gptr, (void *)S->d_gcol, (void *)S->d_gout, (void *)S->d_gk,
+                    (void *)S->d_chi, (void *)S->d_rs, (void *)S->d_xs})
         cudaFree(p);
     delete S;
-    h->sym = nullptr;
 }
 
-// Build the symmetric coupling data from the handle's coupling tasks (device
-// copy of the kept columns) and check S^{s,t} = (S^{t,s})^T on the device.
-h2_status h2_sym_init(h2_handle *h)
+// Build the once-per-pair structure of the couplings (near = false: ids are
+// clusters found by coefficient offset, kept blocks s > t) or of the near
+// field (near = true: ids are leaves found by their first unknown, kept
+// blocks s >= t, the diagonal block only for the direct product; chi has one
+// entry per unknown in tree order). The kept columns are copied on the
+// device and every pair is checked there against its stored partner.
+h2_status build_sym(h2_handle *h, bool near, const std::vector<float2> *chi, SymState **out)
 {
-    if (h->sym) return H2_OK;
-    const Phase &C = h->couple;
+    const Phase &C = near ? h->near : h->couple;
+    const std::string what = near ? "symmetric near field: " : "symmetric couplings: ";
     const std::vector<Seg> &hsegs = h->segs_host;
-    std::unordered_map<int32_t, int32_t> cluster_of_xo;
-    for (int t = 0; t < h->nc; ++t)
-        if (h->rank[t] > 0) cluster_of_xo[h->xo[t]] = t;
+    std::unordered_map<int32_t, int32_t> id;
+    for (int t = 0; t < h->nc; ++t) {
+        if (near && h->child[2 * t] < 0) id[h->begin[t]] = t;
+        if (!near && h->rank[t] > 0) id[h->xo[t]] = t;
+    }
+    auto out_id = [&](const Task &tk) -> int32_t {
+        const auto it = id.find((int32_t)(near ? tk.out_off : tk.out_off - h->ktot));
+        return it == id.end() ? -1 : it->second;
+    };
+    auto seg_id = [&](const Seg &sg) -> int32_t {
+        if (near != (sg.in_off >= 0)) return -1;
+        const auto it = id.find((int32_t)(near ? sg.in_off : -(int64_t)sg.in_off - 1));
+        if (it == id.end() || (near ? h->size[it->second] : h->rank[it->second]) != sg.n) return -1;
+        return it->second;
+    };
     struct Blk {
         int64_t off;
         int32_t mpad, kt, ks;
     };
     std::unordered_map<int64_t, Blk> blocks;   // key t * nc + s
     for (const Task &tk : C.tasks) {
-        const auto it = cluster_of_xo.find((int32_t)(tk.out_off - h->ktot));
-        if (it == cluster_of_xo.end()) return (set_error("symmetric couplings: unknown output cluster"), H2_ERR_STATE);
-        const int32_t t = it->second;
+        const int32_t t = out_id(tk);
+        if (t < 0) return (set_error(what + "unknown output block"), H2_ERR_STATE);
         int col = 0;
         for (int si = tk.seg_begin; si < tk.seg_end; ++si) {
-            const Seg &sg = hsegs[si];
-            const auto is = sg.in_off < 0 ? cluster_of_xo.find((int32_t)(-(int64_t)sg.in_off - 1)) : cluster_of_xo.end();
-            if (is == cluster_of_xo.end() || h->rank[is->second] != sg.n)
-                return (set_error("symmetric couplings: a coupling input is not a cluster's coefficient block"), H2_ERR_STATE);
-            blocks[(int64_t)t * h->nc + is->second] = {tk.mat_off + (int64_t)col * tk.mpad, tk.mpad, tk.m, sg.n};
-            col += sg.n;
+            const int32_t s = seg_id(hsegs[si]);
+            if (s < 0) return (set_error(what + "an input segment is not a whole cluster block"), H2_ERR_STATE);
+            blocks[(int64_t)t * h->nc + s] = {tk.mat_off + (int64_t)col * tk.mpad, tk.mpad, tk.m, hsegs[si].n};
+            col += hsegs[si].n;
         }
     }
-    // kept blocks (s > t) per task, in the handle's task order
+    // kept blocks per task, in the handle's task order
     std::vector<Task> tasks;
     std::vector<Seg> segs;
     std::vector<int64_t> col0, colsrc;
     std::vector<SymPair> pairs;
-    std::vector<std::vector<int64_t>> lower(h->nc);   // per cluster s: first scratch column of each (t, s), t < s
+    std::vector<std::vector<int64_t>> lower(h->nc);   // per id s: first scratch column of each (t, s), t < s
     int64_t mat_elems = 0, ncols = 0, stored = 0;
     for (const Task &tk : C.tasks) {
-        if (tk.mpad > 128) return (set_error("symmetric couplings: ranks above 128 are not supported"), H2_ERR_STATE);
-        const int32_t t = cluster_of_xo.at((int32_t)(tk.out_off - h->ktot));
+        if (tk.mpad > 128) return (set_error(what + "blocks with more than 128 rows are not supported"), H2_ERR_STATE);
+        const int32_t t = out_id(tk);
         Task u = tk;
         u.ncol = 0;
         u.mat_off = mat_elems;
@@ -354,15 +400,21 @@ h2_status h2_sym_init(h2_handle *h)
         const int64_t c0 = ncols;
         for (int si = tk.seg_begin; si < tk.seg_end; ++si) {
             const Seg &sg = hsegs[si];
-            const int32_t s = cluster_of_xo.at((int32_t)(-(int64_t)sg.in_off - 1));
-            if (s <= t) continue;
-            const auto back = blocks.find((int64_t)s * h->nc + t);
-            if (back == blocks.end())
-                return (set_error("symmetric couplings: admissible pair without its transpose"), H2_ERR_STATE);
+            const int32_t s = seg_id(sg);
+            if (s < t || (s == t && !near)) continue;
             const Blk &f = blocks.at((int64_t)t * h->nc + s);
+            if (s > t) {
+                const auto back = blocks.find((int64_t)s * h->nc + t);
+                if (back == blocks.end()) return (set_error(what + "a block pair without its transpose"), H2_ERR_STATE);
+                lower[s].push_back(c0 + u.ncol);
+                SymPair pr{f.off, back->second.off, f.mpad, back->second.mpad, f.kt, f.ks, 0, 0};
+                if (near) {
+                    pr.ra = h->begin[t];
+                    pr.cs = h->begin[s];
+                }
+                pairs.push_back(pr);
+            }
             for (int j = 0; j < sg.n; ++j) colsrc.push_back(f.off + (int64_t)j * f.mpad);
-            lower[s].push_back(c0 + u.ncol);
-            pairs.push_back({f.off, back->second.off, f.mpad, back->second.mpad, f.kt, f.ks});
             segs.push_back(sg);
             u.ncol += sg.n;
             stored += (int64_t)f.kt * f.ks;
@@ -396,20 +448,15 @@ h2_status h2_sym_init(h2_handle *h)
         if (lower[s].empty()) continue;
         gcol.insert(gcol.end(), lower[s].begin(), lower[s].end());
         gptr.push_back((int32_t)gcol.size());
-        gout.push_back((int32_t)(h->ktot + h->xo[s]));
-        gk.push_back(h->rank[s]);
+        gout.push_back((int32_t)(near ? h->begin[s] : h->ktot + h->xo[s]));
+        gk.push_back(near ? h->size[s] : h->rank[s]);
     }
 
     auto *S = new SymState();
-    h->sym = S;
     S->ntask = (int)tasks.size();
     S->ntarget = (int)gout.size();
     S->stored_elems = stored;
     S->scratch_entries = ncols;
-    auto fail = [&](h2_status st) {
-        h2_free_sym(h);
-        return st;
-    };
     auto up = [&](auto &vec, auto **dptr) -> cudaError_t {
         using T = typename std::remove_reference<decltype(vec)>::type::value_type;
         cudaError_t e = cudaMalloc(dptr, std::max<size_t>(1, vec.size()) * sizeof(T));
@@ -424,40 +471,81 @@ h2_status h2_sym_init(h2_handle *h)
         cudaFree(d_pairs);
         cudaFree(d_worst);
     };
+    std::vector<float2> rs;
+    if (near) {
+        rs.resize(chi->size());
+        for (size_t i = 0; i < rs.size(); ++i) {   // 1 / chi
+            const double cr = (*chi)[i].x, ci = (*chi)[i].y, d = cr * cr + ci * ci;
+            rs[i] = make_float2((float)(cr / d), (float)(-ci / d));
+        }
+    }
     cudaError_t e = cudaSuccess;
     if ((e = up(tasks, &S->d_tasks)) != cudaSuccess || (e = up(segs, &S->d_segs)) != cudaSuccess ||
         (e = up(col0, &S->d_col0)) != cudaSuccess || (e = up(gptr, &S->d_gptr)) != cudaSuccess ||
         (e = up(gcol, &S->d_gcol)) != cudaSuccess || (e = up(gout, &S->d_gout)) != cudaSuccess ||
         (e = up(gk, &S->d_gk)) != cudaSuccess || (e = up(colsrc, &d_colsrc)) != cudaSuccess ||
         (e = up(pairs, &d_pairs)) != cudaSuccess ||
+        (near && ((e = up(*chi, &S->d_chi)) != cudaSuccess || (e = up(rs, &S->d_rs)) != cudaSuccess ||
+                  (e = cudaMalloc(&S->d_xs, std::max<size_t>(1, chi->size()) * sizeof(float2))) != cudaSuccess)) ||
         (e = cudaMalloc(&S->d_mat, std::max<int64_t>(32, mat_elems) * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&S->d_scratch, std::max<int64_t>(1, ncols) * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&d_worst, sizeof(unsigned))) != cudaSuccess || (e = cudaMemset(d_worst, 0, sizeof(unsigned))) != cudaSuccess) {
         cudaGetLastError();
         tmp_free();
-        set_error(std::string("symmetric couplings: device allocation failed: ") + cudaGetErrorString(e));
-        return fail(e == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA);
+        free_state(S);
+        set_error(what + "device allocation failed: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA;
     }
     if (S->ntask > 0) symcopy_kernel<<<S->ntask, 256>>>(S->d_tasks, S->d_col0, d_colsrc, h->d_mat, S->d_mat);
-    if (!pairs.empty()) symcheck_kernel<<<(unsigned)pairs.size(), 256>>>(d_pairs, h->d_mat, d_worst);
+    if (!pairs.empty()) symcheck_kernel<<<(unsigned)pairs.size(), 256>>>(d_pairs, h->d_mat, S->d_chi, d_worst);
     unsigned worst = 0;
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(&worst, d_worst, sizeof(unsigned), cudaMemcpyDeviceToHost);
     tmp_free();
     if (e != cudaSuccess) {
         cudaGetLastError();
-        set_error(std::string("symmetric couplings: ") + cudaGetErrorString(e));
-        return fail(H2_ERR_CUDA);
+        free_state(S);
+        set_error(what + cudaGetErrorString(e));
+        return H2_ERR_CUDA;
     }
     float w;
     memcpy(&w, &worst, sizeof(w));
     S->max_asym = w;
     if (!(w <= 1e-5f)) {
-        set_error("symmetric couplings: S^{s,t} differs from (S^{t,s})^T by " + std::to_string(w) +
-                  " relative (limit 1e-5)");
-        return fail(H2_ERR_STATE);
+        free_state(S);
+        set_error(what + "a block differs from its stored partner by " + std::to_string(w) + " relative (limit 1e-5)");
+        return H2_ERR_STATE;
     }
+    *out = S;
     return H2_OK;
+}
+
+}  // namespace
+
+void h2_free_sym(h2_handle *h)
+{
+    free_state(h->sym);
+    h->sym = nullptr;
+    free_state(h->symnear);
+    h->symnear = nullptr;
+}
+
+void symnear_free(h2_handle *h)
+{
+    free_state(h->symnear);
+    h->symnear = nullptr;
+}
+
+h2_status h2_sym_init(h2_handle *h)
+{
+    if (h->sym) return H2_OK;
+    return build_sym(h, false, nullptr, &h->sym);
+}
+
+h2_status symnear_init(h2_handle *h, const std::vector<float2> &chi)
+{
+    symnear_free(h);
+    return build_sym(h, true, &chi, &h->symnear);
 }
 
 // couplings of all levels with the symmetric storage: yh = S xh (FP32)
@@ -465,10 +553,25 @@ cudaError_t h2_sym_couple(h2_handle *h, float2 *coef, cudaStream_t st)
 {
     const SymState *S = h->sym;
     if (S->ntask > 0)
-        symcouple_kernel<<<S->ntask, SYM_THREADS, 0, st>>>(S->d_tasks, S->d_segs, S->d_mat, S->d_col0, coef, h->ktot,
-                                                           S->d_scratch);
+        symcouple_kernel<<<S->ntask, SYM_THREADS, 0, st>>>(S->d_tasks, S->d_segs, S->d_mat, S->d_col0, coef, nullptr,
+                                                           coef, -h->ktot, coef, S->d_scratch);
     if (S->ntarget > 0)
-        symgather_kernel<<<S->ntarget, 128, 0, st>>>(S->d_gptr, S->d_gcol, S->d_gout, S->d_gk, S->d_scratch, coef);
+        symgather_kernel<<<S->ntarget, 128, 0, st>>>(S->d_gptr, S->d_gcol, S->d_gout, S->d_gk, S->d_scratch, nullptr,
+                                                     coef);
+    return cudaGetLastError();
+}
+
+// near field with the symmetric storage: y = Z x (FP32), written, not added
+cudaError_t symnear_run(h2_handle *h, const float2 *x, float2 *y, cudaStream_t st)
+{
+    const SymState *S = h->symnear;
+    symscale_kernel<<<std::max(1, std::min(1024, (h->n + 255) / 256)), 256, 0, st>>>(S->d_chi, x, S->d_xs, h->n);
+    if (S->ntask > 0)
+        symcouple_kernel<<<S->ntask, SYM_THREADS, 0, st>>>(S->d_tasks, S->d_segs, S->d_mat, S->d_col0, x, x, S->d_xs,
+                                                           0, y, S->d_scratch);
+    if (S->ntarget > 0)
+        symgather_kernel<<<S->ntarget, 128, 0, st>>>(S->d_gptr, S->d_gcol, S->d_gout, S->d_gk, S->d_scratch, S->d_rs,
+                                                     y);
     return cudaGetLastError();
 }
 

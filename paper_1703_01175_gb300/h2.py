@@ -94,6 +94,11 @@ def lib() -> ctypes.CDLL:
                                  ctypes.c_int64, ctypes.c_int]
     L.h2_get_stats.restype = ctypes.c_int
     L.h2_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Stats)]
+    L.h2_sym_near.restype = ctypes.c_int
+    L.h2_sym_near.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    L.h2_sym_near_stats.restype = ctypes.c_int
+    L.h2_sym_near_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_double)]
     L.h2_sym_stats.restype = ctypes.c_int
     L.h2_sym_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double)]
@@ -134,7 +139,7 @@ def _check(status: int, where: str):
 
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
-    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats",
+    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats", "h2_sym_near", "h2_sym_near_stats",
             "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_autotune",
             "h2_status_string", "h2_last_error"]
 
@@ -298,6 +303,25 @@ class H2Matrix:
         s = _Stats()
         _check(lib().h2_get_stats(self._h, ctypes.byref(s)), "h2_get_stats")
         return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def sym_near(self, chi):
+        """Store the near field once per leaf pair for the single-RHS FP32
+        product; chi: numpy complex array (n,) in tree order, or None to go
+        back to the full storage."""
+        if chi is None:
+            _check(lib().h2_sym_near(self._h, None, H2_C128), "h2_sym_near")
+            return
+        c = np.ascontiguousarray(chi, dtype=np.complex128)
+        if c.shape != (self.n,):
+            raise ValueError(f"chi must have shape ({self.n},)")
+        _check(lib().h2_sym_near(self._h, c.ctypes.data, H2_C128), "h2_sym_near")
+
+    def sym_near_stats(self) -> dict:
+        """Near field stored once per leaf pair (after sym_near)."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        _check(lib().h2_sym_near_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "h2_sym_near_stats")
+        return {"stored_elems": a.value, "scratch_entries": b.value, "max_asym": c.value}
 
     def sym_stats(self) -> dict:
         """Symmetric coupling storage (handle loaded with sym_couple=True)."""

@@ -12,7 +12,7 @@ the H^2 data of the host constructor, the launch configuration bench.py times.
   smaller 16^3 version), so the solves use m = 400;
 - split-bf16 products of 8 right-hand sides: sampled columns within eps;
 - double-float and FP64 accumulation agree to 1e-12;
-- couplings stored once per admissible pair: within 1e-6 of full storage.
+- couplings and near blocks stored once per pair: within 1e-6 of full storage.
 """
 import math
 
@@ -131,5 +131,11 @@ def test_full_size_symmetric_couplings(full):
         assert np.linalg.norm(ys - yf) <= 1e-6 * np.linalg.norm(yf)
         yo = h2mv.h2_matvec(hZ, x.astype(np.complex64).astype(np.complex128))
         assert np.linalg.norm(ys - yo) <= 1e-5 * np.linalg.norm(yo)
+        # and the near field once per leaf pair (chi of the workload, nowhere zero)
+        B.sym_near(np.repeat(np.asarray(w.voxels.eps_r, dtype=np.complex128)[perm] - 1.0, 3))
+        assert B.sym_near_stats()["max_asym"] <= 1e-5
+        yn = B.matvec(xt).cpu().numpy()
+        assert np.linalg.norm(yn - yf) <= 1e-6 * np.linalg.norm(yf)
+        assert np.linalg.norm(yn - yo) <= 1e-5 * np.linalg.norm(yo)
     finally:
         B.close()

@@ -315,3 +315,54 @@ def test_symmetric_couplings_after_reload(loaded, tmp_path):
             B.close()
     finally:
         A.close()
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_symmetric_near_field_matches_oracle(loaded, name):
+    """Near field stored once per leaf pair (with the couplings once per
+    pair): stores the diagonal blocks and one block of each pair, matches
+    the oracle within 1e-5 and the full-storage product within 1e-6, replays
+    bitwise, and h2_sym_near(NULL) returns to the couplings-only product."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get(name)
+    full = _mat(loaded, name)
+    arrs = c.arrays()
+    A = h2.H2Matrix(arrs, sym_couple=True)
+    try:
+        x = synth.random_complex(c.n, 7)
+        xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+        y_cpl = A.matvec(xt).clone()
+        A.sym_near(c.chi)
+        st = A.sym_near_stats()
+        leaves = np.asarray(arrs.child).reshape(-1, 2)[:, 0] < 0
+        diag = int(np.sum(np.asarray(arrs.size, dtype=np.int64)[leaves] ** 2))
+        assert 2 * st["stored_elems"] == full.stats()["near_elems"] + diag
+        assert st["max_asym"] <= 1e-5
+        y1 = A.matvec(xt).clone()
+        assert torch.equal(y1, A.matvec(xt))
+        y = y1.cpu().numpy()
+        assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+        assert _rel(y, full.matvec(xt).cpu().numpy()) <= 1e-6
+        A.sym_near(None)
+        assert torch.equal(A.matvec(xt), y_cpl)
+    finally:
+        A.close()
+
+
+def test_symmetric_near_field_refuses_zero_chi(loaded):
+    """A zero chi (void voxel) leaves the near field in full storage with
+    H2_ERR_STATE; products keep working."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube8")
+    A = h2.H2Matrix(c.arrays())
+    try:
+        chi = c.chi.copy()
+        chi[5] = 0.0
+        with pytest.raises(h2.H2Error) as e:
+            A.sym_near(chi)
+        assert e.value.status == 7   # H2_ERR_STATE
+        x = synth.random_complex(c.n, 8)
+        y = A.matvec(torch.from_numpy(x.astype(np.complex64)).cuda()).cpu().numpy()
+        assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+    finally:
+        A.close()

@@ -319,16 +319,6 @@ __global__ void symcheck_kernel(const SymPair *__restrict__ pairs, const float2 
 
 }  // namespace
 
-#define SY_CUDA(call)                                                                 \
-    do {                                                                              \
-        cudaError_t e__ = (call);                                                     \
-        if (e__ != cudaSuccess) {                                                     \
-            cudaGetLastError();                                                       \
-            set_error(std::string("symmetric couplings: ") + #call + ": " + cudaGetErrorString(e__)); \
-            return e__ == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA;    \
-        }                                                                             \
-    } while (0)
-
 namespace {
 
 void free_state(SymState *S)

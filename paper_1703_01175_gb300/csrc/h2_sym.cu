@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <type_traits>
 #include <unordered_map>
@@ -526,16 +527,28 @@ void symnear_free(h2_handle *h)
     h->symnear = nullptr;
 }
 
+// host tables are built with std containers: an allocation failure becomes
+// H2_ERR_ALLOC instead of an exception crossing the C boundary
+static h2_status build_sym_safe(h2_handle *h, bool near, const std::vector<float2> *chi, SymState **out)
+{
+    try {
+        return build_sym(h, near, chi, out);
+    } catch (const std::bad_alloc &) {
+        set_error(near ? "symmetric near field: host allocation failed" : "symmetric couplings: host allocation failed");
+        return H2_ERR_ALLOC;
+    }
+}
+
 h2_status h2_sym_init(h2_handle *h)
 {
     if (h->sym) return H2_OK;
-    return build_sym(h, false, nullptr, &h->sym);
+    return build_sym_safe(h, false, nullptr, &h->sym);
 }
 
 h2_status symnear_init(h2_handle *h, const std::vector<float2> &chi)
 {
     symnear_free(h);
-    return build_sym(h, true, &chi, &h->symnear);
+    return build_sym_safe(h, true, &chi, &h->symnear);
 }
 
 // couplings of all levels with the symmetric storage: yh = S xh (FP32)

@@ -7,7 +7,10 @@
 - leaf ranks equal the SVD rank of G_(t) formed independently here, and the
   non-leaf ranks of the projected construction stay within two of the SVD rank
   of the unprojected G_(t) -- the paper's minimal-rank claim (Abstract,
-  Sec. III.B-C).
+  Sec. III.B-C);
+- the relations that storing blocks once per pair relies on: couplings
+  S^{s,t} = (S^{t,s})^T (Eq. 8, one basis per cluster, K complex symmetric)
+  and near blocks Z^{s,t} = diag(1/chi_s) (Z^{t,s})^T diag(chi_t), t != s.
 """
 import math
 
@@ -132,3 +135,27 @@ def test_minimal_rank_claim(case, request):
             assert hK.rank[t] == r_svd
         else:
             assert abs(int(hK.rank[t]) - r_svd) <= 2
+
+
+@pytest.mark.parametrize("case", ["cube8", "ragged"])
+def test_pairwise_symmetry_of_stored_blocks(case, request):
+    """Couplings of the system H^2 are transposes of each other per pair, and
+    the near blocks of a pair are related through chi; checked on the FP64
+    oracle data, so that a missing transpose or a chi on the wrong side of a
+    block fails here."""
+    Kt, tr, pa, hK, hZ, Zt = request.getfixturevalue(case)
+    chi = np.diag(np.eye(tr.n) - Zt) / np.diag(Kt)   # recover chi from the dense forms
+    n_pairs = 0
+    for (t, s), S in hZ.S.items():
+        if t < s and S.size:
+            assert np.abs(hZ.S[(s, t)] - S.T).max() <= 1e-12 * max(1.0, np.abs(S).max())
+            n_pairs += 1
+    assert n_pairs > 0
+    n_near = 0
+    for (t, s), Z in hZ.Z.items():
+        if t < s:
+            rt, rs = tr.rows(t), tr.rows(s)
+            partner = (Z.T * chi[rt][None, :]) / chi[rs][:, None]
+            assert np.abs(hZ.Z[(s, t)] - partner).max() <= 1e-12 * np.abs(Z).max()
+            n_near += 1
+    assert n_near > 0

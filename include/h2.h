@@ -329,8 +329,9 @@ typedef struct {
  * right-hand sides are solved one after another. info: host array of nrhs
  * entries (may be NULL). Returns H2_OK when every right-hand side converged,
  * else the first failing status. Synchronises `stream` (convergence is read
- * back once per Arnoldi step). Device workspace (N x (m+1) c128 basis) is
- * allocated on first use and kept by the handle.
+ * back once per Arnoldi step). Device workspace (an N x (m+1) basis: 16
+ * bytes per entry for arnoldi 0 and 1, 8 for arnoldi 2) is allocated on first
+ * use and kept by the handle.
  */
 h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld,
                    const h2_solve_opts *opts, h2_solve_info *info, void *stream);
@@ -339,15 +340,18 @@ h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t l
  * Batched restarted GMRES(m): the nrhs right-hand sides advance in lockstep,
  * each with its own Krylov basis, Hessenberg matrix and Givens rotations, so
  * every Arnoldi step runs ONE multi-RHS product (prec = H2_PREC_FP32: CUDA-core
- * complex GEMMs; H2_PREC_SPLITBF16: tensor cores) and the FP64 Gram-Schmidt
- * (selective reorthogonalisation, as in h2_gmres), rotation and
- * back-substitution kernels are batched over the right-hand sides. A right-hand side whose residual estimate drops below
- * tol / 2 stops contributing at the end of the cycle. Restart residuals:
- * FP64-accumulated products when opts->refine (one per right-hand side),
- * else one batched product with `prec`. opts->precond must be 0.
+ * complex GEMMs; H2_PREC_SPLITBF16: tensor cores) and the Gram-Schmidt passes
+ * (arithmetic by opts->arnoldi, selective reorthogonalisation, as in
+ * h2_gmres) are batched over the right-hand sides; the Hessenberg columns,
+ * rotations and back-substitution run in FP64 on the host. A right-hand side
+ * whose residual estimate drops below tol / 2 stops contributing at the end
+ * of the cycle. Restart residuals: accumulated products when opts->refine
+ * (one per right-hand side; FP64ACC for arnoldi 0, DFACC for 1 and 2), else
+ * one batched product with `prec`. opts->precond must be 0.
  * b, x: device c128, nrhs columns with leading dimension ld >= N.
- * Workspace: N x (m+1) x nrhs c128 basis plus O(N nrhs) vectors, allocated
- * on first use and kept by the handle. Synchronises `stream` once per step.
+ * Workspace: an N x (m+1) x nrhs basis (16 bytes per entry for arnoldi 0
+ * and 1, 8 for arnoldi 2) plus O(N nrhs) vectors, allocated on first use and
+ * kept by the handle. Synchronises `stream` once per step.
  */
 h2_status h2_gmres_batched(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t ld,
                            const h2_solve_opts *opts, h2_prec prec, h2_solve_info *info, void *stream);

@@ -87,6 +87,10 @@ def test_null_arguments():
     assert h.value is None
     assert L.h2_matvec(None, None, None, 1, 1, 0, None) == h2py.H2_ERR_ARG
     L.h2_free(None)
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    assert L.h2_sym_stats(None, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == h2py.H2_ERR_ARG
+    assert L.h2_sym_near(None, None, 1) == h2py.H2_ERR_ARG
+    assert L.h2_sym_near_stats(None, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == h2py.H2_ERR_ARG
 
 
 def test_load_file_rejects_foreign_and_corrupted_files(tmp_path):

@@ -160,12 +160,13 @@ void h2_free(h2_handle *h);
  * must not overlap x. Element type: c64 for H2_PREC_FP32 / H2_PREC_SPLITBF16,
  * c128 for H2_PREC_FP64ACC / H2_PREC_DFACC. nrhs >= 1.
  * Paths: nrhs = 1 FP32 runs level-batched GEMVs; nrhs > 1 FP32 runs complex
- * GEMMs on CUDA cores; H2_PREC_SPLITBF16 runs the near-field and coupling
- * products on the tensor cores (tcgen05, operands split into two bf16 terms,
- * FP32 accumulation; relative error ~1e-5) and the tree passes in FP32. The
- * first split-bf16 call packs the tensor-core operand images (device memory
- * about twice the FP32 near-field and coupling data). FP64ACC with nrhs > 1
- * runs one right-hand side after another.
+ * GEMMs on CUDA cores; H2_PREC_SPLITBF16 runs every pass -- leaf forward
+ * transforms, upward transfers, couplings merged with the downward transfers,
+ * and the near field merged with the leaf expansion -- on the tensor cores
+ * (tcgen05, operands split into two bf16 terms, FP32 accumulation in tensor
+ * memory; relative error ~1e-5). The first split-bf16 call packs the
+ * tensor-core operand images of every stored matrix. FP64ACC and DFACC with
+ * nrhs > 1 run one right-hand side after another.
  * Asynchronous on `stream`. Not thread-safe on one handle.
  */
 h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs,
@@ -255,17 +256,19 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
  * (8 MiB) that every GPU loading the library holds until the process exits.
  * The paper has no counterpart; this entry point exists for callers that must
  * not call the CUDA allocator once running -- a step embedded in another
- * framework whose caching allocator owns the device memory, a real-time loop
- * that cannot take cudaMalloc's implicit synchronisation, or work issued
- * while a stream is being captured into a graph. Such a caller loads the
- * operator with h2_load at initialisation and afterwards passes only x and y.
+ * framework whose caching allocator owns the device memory, or a real-time
+ * loop that cannot take cudaMalloc's implicit synchronisation. Such a caller
+ * loads the operator with h2_load at initialisation and afterwards passes
+ * only x and y. This path always uses the full block storage (the symmetric
+ * storage of sym_couple and h2_sym_near is not used here).
  * Operators needing more than H2_NOALLOC_MAX_COEF coefficients (2 x the sum
- * of the cluster ranks) are rejected with H2_ERR_ARG. The first call on a
- * device looks up the array's device address (once per device); make that
- * first call before any stream capture. Every call shares the one array:
- * calls that overlap on the GPU (different streams, or concurrent host
- * threads) race and give wrong results. The array is zeroed at the start of
- * every call. Asynchronous on `stream`.
+ * of the cluster ranks) are rejected with H2_ERR_ARG before any device work.
+ * The first call on a handle looks up the array's device address in the
+ * handle's context and keeps it in the handle; make that first call before
+ * any stream capture. Every call shares the one array: calls that overlap on
+ * the GPU (different streams, or concurrent host threads) race and give
+ * wrong results. The array keeps the previous call's values, so every call
+ * zeroes it first. Asynchronous on `stream`.
  */
 #define H2_NOALLOC_MAX_COEF 1048576
 h2_status h2_matvec_noalloc(h2_handle *h, const void *x, void *y, void *stream);
@@ -318,10 +321,12 @@ typedef struct {
 
 /*
  * Solve A x = b by restarted GMRES(m) (Saad & Schultz) around the H^2
- * product: FP64 Arnoldi on c128 vectors (classical Gram-Schmidt with selective
- * reorthogonalisation: a second projection when the first one cancels more
- * than half of |w|^2), Givens rotations and the Hessenberg least-squares solve
- * on the device, FP32 H^2 products inside the cycles. Each restart recomputes the
+ * product: Arnoldi on the device (arithmetic by opts->arnoldi; classical
+ * Gram-Schmidt with selective reorthogonalisation: a second projection when
+ * the first one leaves |w'| < eta |w|), FP32 H^2 products inside the cycles;
+ * the projection coefficients of each step are copied to the host, where the
+ * Hessenberg column, the Givens rotations, the residual estimate and the
+ * least-squares back-substitution run in FP64. Each restart recomputes the
  * true residual (FP64-accumulated product when opts->refine). The paper's own
  * solver is BiCGStab (Sec. V); this is the Krylov method around the same
  * product (Sec. IV.B).

@@ -78,14 +78,3 @@ def h2_dense(h2: H2) -> np.ndarray:
     for (t, s), Zb in h2.Z.items():
         A[np.ix_(tree.rows(t), tree.rows(s))] += Zb
     return A
-
-
-def storage_counts(h2: H2) -> dict:
-    """Complex entries stored per kind (Sec. IV.A, Eq. 19)."""
-    tree = h2.tree
-    near = sum(b.size for b in h2.Z.values())
-    adm = sum(b.size for b in h2.S.values())
-    transfer = sum(b.size for b in h2.T.values())
-    leaf = sum(b.size for b in h2.U.values())
-    return {"near": near, "coupling": adm, "transfer": transfer, "leaf": leaf,
-            "n": tree.n}

@@ -284,7 +284,8 @@ static h2_status upload_and_finish(h2_handle *h, int device, const float2 *mat, 
         set_error("no CUDA device " + std::to_string(device));
         return fail(H2_ERR_CUDA);
     }
-    if (cudaSetDevice(device) != cudaSuccess) return fail(H2_ERR_CUDA);
+    DeviceGuard dev_guard(device);
+    if (dev_guard.err != cudaSuccess) return fail(H2_ERR_CUDA);
 #define H2_LOAD_CUDA(call)                                                         \
     do {                                                                           \
         cudaError_t e__ = (call);                                                  \
@@ -606,7 +607,8 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
 h2_status h2_device_status(h2_handle *h)
 {
     if (!h) return arg_error("h2_device_status: NULL handle");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     H2_CUDA(cudaDeviceSynchronize());
     int flag = 0;
     h2_status s = h2_split_error_flag(h, &flag);
@@ -666,7 +668,8 @@ struct Reader {
 h2_status h2_save(const h2_handle *h, const char *path)
 {
     if (!h || !path) return arg_error("h2_save: NULL argument");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     FILE *f = fopen(path, "wb");
     if (!f) return arg_error(std::string("h2_save: cannot open ") + path);
     Writer w{f};
@@ -840,7 +843,8 @@ h2_status h2_sym_stats(h2_handle *h, int64_t *stored_elems, int64_t *scratch_ent
 {
     if (!h || !stored_elems || !scratch_entries || !max_asym) return arg_error("h2_sym_stats: NULL argument");
     if (!h->sym_couple) return (set_error("h2_sym_stats: the handle was loaded without sym_couple=1"), H2_ERR_STATE);
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     if (!h->sym) {
         const h2_status s = h2::h2_sym_init(h);
         if (s != H2_OK) return s;
@@ -945,7 +949,8 @@ h2_status h2_sym_near(h2_handle *h, const void *chi, h2_dtype dtype)
 {
     if (!h) return arg_error("h2_sym_near: NULL handle");
     if (chi && dtype != H2_C64 && dtype != H2_C128) return arg_error("h2_sym_near: bad dtype");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     H2_CUDA(cudaDeviceSynchronize());
     drop_graphs(h);   // captured products use the previous near-field structure
     if (!chi) {
@@ -994,7 +999,8 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
     if (x == y) return arg_error("h2_matvec: x and y must not overlap");
     if (prec != H2_PREC_FP32 && prec != H2_PREC_FP64ACC && prec != H2_PREC_SPLITBF16 && prec != H2_PREC_DFACC)
         return arg_error("h2_matvec: bad precision");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (prec == H2_PREC_SPLITBF16)
         return h2_run_multi_split(h, reinterpret_cast<const float2 *>(x), nrhs > 1 ? ld : h->n,
@@ -1029,7 +1035,8 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host, int32_t
     if (ld < h->n) return arg_error("h2_matvec_host: ld < n");
     const size_t esz = (prec == H2_PREC_FP64ACC || prec == H2_PREC_DFACC) ? sizeof(double2) : sizeof(float2);
     const int64_t bytes = (int64_t)esz * ld * nrhs;
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     if (bytes > h->buf_bytes) {
         cudaFree(h->d_xbuf);
         cudaFree(h->d_ybuf);
@@ -1054,7 +1061,8 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host, int32_t
 h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters, double *ms, int32_t n_ms)
 {
     if (!h || !x || !y || !ms || iters < 1 || n_ms < 1) return arg_error("h2_profile_matvec: bad argument");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     if (h->sym_couple && !h->sym) {
         const h2_status s = h2::h2_sym_init(h);
         if (s != H2_OK) return s;
@@ -1063,8 +1071,17 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
     const float2 *xx = reinterpret_cast<const float2 *>(x);
     float2 *yy = reinterpret_cast<float2 *>(y);
     float2 *coef = reinterpret_cast<float2 *>(h->d_coef);
-    cudaEvent_t ev[7];
-    for (auto &e : ev) H2_CUDA(cudaEventCreate(&e));
+    // the events are released on every return path
+    struct Events {
+        cudaEvent_t e[7] = {};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    cudaEvent_t *ev = evs.e;
+    for (int k = 0; k < 7; ++k) H2_CUDA(cudaEventCreate(&ev[k]));
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int it = 0; it <= iters; ++it) {
         H2_CUDA(cudaMemsetAsync(coef, 0, sizeof(float2) * 2 * std::max<int64_t>(1, h->ktot), st));
@@ -1104,7 +1121,6 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
     float f = 0;
     H2_CUDA(cudaEventElapsedTime(&f, ev[0], ev[1]));
     acc[6] = f;
-    for (auto &e : ev) cudaEventDestroy(e);
     for (int k = 0; k < n_ms && k < 7; ++k) ms[k] = acc[k] / iters;
     return H2_OK;
 }
@@ -1118,7 +1134,8 @@ h2_status h2_profile_matvec(h2_handle *h, const void *x, void *y, int32_t iters,
 extern "C" h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len)
 {
     if (!h) return arg_error("h2_autotune: NULL handle");
-    H2_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
     cudaStream_t st = h->s_aux;
     float2 *xb = nullptr, *yb = nullptr;
     if (cudaMalloc(&xb, sizeof(float2) * h->n) != cudaSuccess || cudaMalloc(&yb, sizeof(float2) * h->n) != cudaSuccess) {

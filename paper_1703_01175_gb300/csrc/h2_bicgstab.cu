@@ -301,7 +301,8 @@ extern "C" h2_status h2_bicgstab(h2_handle *h, const void *b_, void *x_, int32_t
     if (opts->precond) return (set_error("h2_bicgstab: no preconditioner in BiCGStab"), H2_ERR_ARG);
     if (opts->arnoldi != ARN_FP64 && opts->arnoldi != ARN_DF)
         return (set_error("h2_bicgstab: unknown residual arithmetic"), H2_ERR_ARG);
-    BGC(cudaSetDevice(h->device));
+    h2::DeviceGuard dev_guard(h->device);
+    BGC(dev_guard.err);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     BGWork *w = nullptr;
     h2_status s = bg_get(h, &w);

@@ -51,7 +51,8 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
     if (prec != H2_PREC_FP32 && prec != H2_PREC_SPLITBF16)
         return (set_error("h2_gmres_batched: products must be H2_PREC_FP32 or H2_PREC_SPLITBF16"), H2_ERR_ARG);
     if (opts->precond) return (set_error("h2_gmres_batched: no preconditioner in the batched solver"), H2_ERR_ARG);
-    if (cudaSetDevice(h->device) != cudaSuccess) return (set_error("h2_gmres_batched: cudaSetDevice failed"), H2_ERR_CUDA);
+    h2::DeviceGuard dev_guard(h->device);
+    if (dev_guard.err != cudaSuccess) return (set_error("h2_gmres_batched: cudaSetDevice failed"), H2_ERR_CUDA);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ArnWork *w = reinterpret_cast<ArnWork *>(h->bkrylov);
     h2_status s = arn_get(&w, h->n, m, nrhs, 0, opts->arnoldi);

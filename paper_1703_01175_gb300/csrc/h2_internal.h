@@ -99,6 +99,28 @@ struct SplitState {
 
 void set_error(const std::string &msg);
 
+// Makes a device current for the lifetime of the guard and restores the
+// caller's current device when it goes out of scope, so that no entry point
+// changes the calling thread's device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            prev = -1;
+            cudaGetLastError();
+        }
+        err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // Couplings stored once per admissible pair (h2_sym.cu): tasks hold the blocks
 // S^{t,s} with s > t; scratch holds (S^{t,s})^T xh^t, one entry per stored
 // column; gather lists add those into yh^s.
@@ -228,6 +250,9 @@ struct h2_handle {
     bool sym_couple = false;          // single-RHS FP32 product: couplings stored once per pair
     h2::SymState *sym = nullptr;      // built on first use (h2_sym.cu)
     h2::SymState *symnear = nullptr;  // near field stored once per leaf pair (h2_sym_near)
+    // device address of the static scratch array of h2_matvec_noalloc in the
+    // context that owns this handle's memory (looked up by the first such call)
+    float2 *noalloc_coef = nullptr;
 };
 
 void h2_free_krylov(h2_handle *h);

@@ -57,7 +57,8 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
     const bool flexible = opts->precond != 0;
     if (flexible && !h->precond)
         return (set_error("h2_gmres: no preconditioner loaded (h2_set_preconditioner)"), H2_ERR_STATE);
-    if (cudaSetDevice(h->device) != cudaSuccess) return (set_error("h2_gmres: cudaSetDevice failed"), H2_ERR_CUDA);
+    h2::DeviceGuard dev_guard(h->device);
+    if (dev_guard.err != cudaSuccess) return (set_error("h2_gmres: cudaSetDevice failed"), H2_ERR_CUDA);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ArnWork *w = reinterpret_cast<ArnWork *>(h->krylov);
     h2_status s = arn_get(&w, h->n, m, 1, flexible ? m : 0, opts->arnoldi);

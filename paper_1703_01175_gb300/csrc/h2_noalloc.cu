@@ -3,19 +3,16 @@
 //
 // Who needs it: code that runs where the CUDA allocator must not be called.
 // Examples are a solver step embedded in another framework whose caching
-// allocator has reserved all device memory, a control loop with a real-time
-// budget where cudaMalloc's implicit device synchronisation is not allowed,
-// or a product launched while its stream is being captured into a CUDA graph
-// (cudaMalloc is not a capturable operation). Such a caller loads the operator
-// once at initialisation (h2_load allocates) and from then on only passes
-// x and y.
+// allocator has reserved all device memory, or a control loop with a
+// real-time budget where cudaMalloc's implicit device synchronisation is not
+// allowed. Such a caller loads the operator once at initialisation (h2_load
+// allocates) and from then on only passes x and y.
 //
 // The scratch holds the forward-transform coefficients xh and the backward
 // coefficients yh (2 * sum of ranks complex64 entries). It is one array per
 // GPU that loads the library, kept until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "h2_internal.h"
@@ -24,29 +21,23 @@ static __device__ __align__(256) float2 g_h2_noalloc_scratch[H2_NOALLOC_MAX_COEF
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-float2 *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
-h2_status scratch_address(int device, float2 **out)
+// Device address of the scratch array in the current context. The host-side
+// symbol is only a stand-in and must never reach a kernel; the address is
+// looked up with the handle's device current and kept in the handle, whose
+// memory lives in that same context.
+h2_status scratch_address(h2_handle *h, float2 **out)
 {
-    if (device < 0 || device >= kMaxDevices) {
-        h2::set_error("h2_matvec_noalloc: device index out of range");
-        return H2_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[device]) {
+    if (!h->noalloc_coef) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_h2_noalloc_scratch);
         if (e != cudaSuccess || !p) {
+            cudaGetLastError();
             h2::set_error(std::string("h2_matvec_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             return H2_ERR_CUDA;
         }
-        g_scratch_ptr[device] = reinterpret_cast<float2 *>(p);
+        h->noalloc_coef = reinterpret_cast<float2 *>(p);
     }
-    *out = g_scratch_ptr[device];
+    *out = h->noalloc_coef;
     return H2_OK;
 }
 
@@ -79,9 +70,10 @@ extern "C" h2_status h2_matvec_noalloc(h2_handle *h, const void *x, void *y, voi
                   std::to_string((long long)H2_NOALLOC_MAX_COEF));
         return H2_ERR_ARG;
     }
-    NA_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dev_guard(h->device);
+    NA_CUDA(dev_guard.err);
     float2 *coef = nullptr;
-    h2_status s = scratch_address(h->device, &coef);
+    h2_status s = scratch_address(h, &coef);
     if (s != H2_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float2 *xx = reinterpret_cast<const float2 *>(x);

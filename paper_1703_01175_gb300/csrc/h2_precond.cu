@@ -157,7 +157,8 @@ extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy,
         h2::set_error("h2_set_preconditioner: the last layer must have 8 output channels");
         return H2_ERR_ARG;
     }
-    if (cudaSetDevice(h->device) != cudaSuccess) return H2_ERR_CUDA;
+    h2::DeviceGuard dev_guard(h->device);
+    if (dev_guard.err != cudaSuccess) return H2_ERR_CUDA;
     h2_free_precond(h);
     auto *P = new PrecondState();
     P->Dx = Dx;

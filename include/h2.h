@@ -135,6 +135,18 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts,
                   h2_handle **out);
 
 /*
+ * As h2_load, with the block arrays of `data` (U, W, T, S, Z) in DEVICE
+ * memory of the target device and of type H2_C64; the tree, the offset and
+ * CSR arrays stay host arrays. Validation is the same; the blocks are packed
+ * on the device (the non-finite check runs there too), so the H^2 data of a
+ * large operator -- built on the GPU by the constructor -- never crosses to the
+ * host. The caller keeps ownership of the block arrays and may free them when
+ * the call returns. Synchronous.
+ */
+h2_status h2_load_device(const h2_tree *tree, const h2_data *data, const char *opts,
+                         h2_handle **out);
+
+/*
  * Write a loaded operator to a file and read it back without re-validating or
  * re-packing the blocks: the tree, the packed task and segment tables and the
  * FP32 device matrices, followed by an FNV-1a hash of the contents (file

@@ -1,6 +1,8 @@
 """Compile the native libraries of the package in-tree.
 
 libh2.so       CUDA C-ABI library (csrc/*.cu), sm_103a only.
+libh2con.so    GPU kernels of the H^2 constructor (csrc_con/*.cu), sm_103a only.
+libh2build.so  host constructor helpers (csrc_host/*.cpp).
 
 Each translation unit is compiled by its own nvcc process in parallel and the
 objects are linked into a shared library next to this file. Rebuilds only when
@@ -22,6 +24,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBH2 = os.path.join(HERE, "libh2.so")
 CSRC_HOST = os.path.join(HERE, "csrc_host")
 LIBH2BUILD = os.path.join(HERE, "libh2build.so")
+CSRC_CON = os.path.join(HERE, "csrc_con")
+LIBH2CON = os.path.join(HERE, "libh2con.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
@@ -42,17 +46,18 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build_libh2(verbose: bool = False, force: bool = False) -> str:
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    hdrs = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")))
-    if not force and not _stale(LIBH2, srcs + hdrs + [__file__]):
-        return LIBH2
+def build_libh2(verbose: bool = False, force: bool = False, srcdir: str = CSRC, target: str = LIBH2) -> str:
+    srcs = sorted(glob.glob(os.path.join(srcdir, "*.cu")))
+    hdrs = sorted(glob.glob(os.path.join(srcdir, "*.h")) + glob.glob(os.path.join(srcdir, "*.cuh"))
+                  + glob.glob(os.path.join(INCLUDE, "*.h")))
+    if not force and not _stale(target, srcs + hdrs + [__file__]):
+        return target
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     procs = []
     objs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + ".o")
+        o = os.path.join(BUILD, os.path.basename(os.path.dirname(s)) + "_" + os.path.basename(s) + ".o")
         objs.append(o)
         cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o]
         if verbose:
@@ -67,13 +72,18 @@ def build_libh2(verbose: bool = False, force: bool = False) -> str:
             print(out.decode(errors="replace"), file=sys.stderr)
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    tmp = LIBH2 + ".tmp"
+    tmp = target + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lgomp"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIBH2)
-    return LIBH2
+    os.replace(tmp, target)
+    return target
+
+
+def build_libh2con(verbose: bool = False, force: bool = False) -> str:
+    """GPU kernels of the H^2 constructor (setup)."""
+    return build_libh2(verbose, force, CSRC_CON, LIBH2CON)
 
 
 def build_libh2build(verbose: bool = False, force: bool = False) -> str:
@@ -96,11 +106,11 @@ def build_libh2build(verbose: bool = False, force: bool = False) -> str:
 
 def build_all(verbose: bool = False, force: bool = False) -> None:
     from concurrent.futures import ThreadPoolExecutor
-    with ThreadPoolExecutor(2) as ex:
-        a = ex.submit(build_libh2, verbose, force)
-        b = ex.submit(build_libh2build, verbose, force)
-        a.result()
-        b.result()
+    with ThreadPoolExecutor(3) as ex:
+        futs = [ex.submit(build_libh2, verbose, force), ex.submit(build_libh2build, verbose, force),
+                ex.submit(build_libh2con, verbose, force)]
+        for f in futs:
+            f.result()
 
 
 if __name__ == "__main__":

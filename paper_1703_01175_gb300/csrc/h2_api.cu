@@ -347,7 +347,36 @@ static h2_status upload_and_finish(h2_handle *h, int device, const float2 *mat, 
     return H2_OK;
 }
 
-h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out)
+}  // extern "C"
+
+// Device packing of h2_load_device: one piece of a task matrix copied from the
+// caller's device block (column-major rows x cols, optionally transposed)
+// into the task's column range of the packed matrix.
+struct DevPiece {
+    const float2 *src;
+    int64_t dst;          // element offset of the piece's first column in the packed matrix
+    int32_t rows, cols;   // source block shape
+    int32_t mpad;         // leading dimension of the packed task matrix
+    int32_t transpose;
+};
+
+__global__ void dev_pack_kernel(const DevPiece *__restrict__ pieces, float2 *__restrict__ mat, int *__restrict__ bad)
+{
+    const DevPiece P = pieces[blockIdx.x];
+    const int orows = P.transpose ? P.cols : P.rows, ocols = P.transpose ? P.rows : P.cols;
+    const int64_t total = (int64_t)orows * ocols;
+    int nonfinite = 0;
+    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int r = (int)(e % orows), j = (int)(e / orows);
+        const float2 v = P.transpose ? P.src[(int64_t)r * P.rows + j] : P.src[(int64_t)j * P.rows + r];
+        nonfinite |= !(isfinite(v.x) && isfinite(v.y));
+        mat[P.dst + (int64_t)j * P.mpad + r] = v;
+    }
+    if (nonfinite) atomicExch(bad, 1);
+}
+
+static h2_status load_impl(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out,
+                           bool on_device)
 {
     if (!out) return arg_error("out is NULL");
     *out = nullptr;
@@ -356,6 +385,7 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     if (st != H2_OK) return st;
     st = validate_data(tree, data, parent);
     if (st != H2_OK) return st;
+    if (on_device && data->dtype != H2_C64) return arg_error("h2_load_device: blocks must be complex64");
 
     int device = 0;
     bool use_graphs = true, tc_pipeline = true, sym_couple = false;
@@ -531,6 +561,29 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         return arg_error("too many blocks");
     }
     std::vector<float2> hmat;
+    std::vector<DevPiece> dpieces;
+    bool finite = true;
+    if (on_device) {
+        // the pieces are copied on the device after the upload step allocated the matrix
+        for (auto &ph : phases)
+            for (const TaskBuild &tb : ph) {
+                int64_t col = 0;
+                for (const Piece &pc : tb.pieces) {
+                    const void *base = pc.kind == 0 ? data->Z : pc.kind == 1 ? data->U : pc.kind == 2 ? data->W
+                                                                : pc.kind == 3 ? data->T : data->S;
+                    DevPiece d;
+                    d.src = reinterpret_cast<const float2 *>(base) + pc.off;
+                    d.dst = tb.t.mat_off + col * tb.t.mpad;
+                    d.rows = pc.rows;
+                    d.cols = pc.cols;
+                    d.mpad = tb.t.mpad;
+                    d.transpose = pc.transpose ? 1 : 0;
+                    if ((int64_t)pc.rows * pc.cols > 0) dpieces.push_back(d);
+                    col += pc.transpose ? pc.rows : pc.cols;
+                }
+            }
+    }
+    if (!on_device) {
     try {
         hmat.assign((size_t)std::max<int64_t>(mat_elems, 32), make_float2(0.f, 0.f));
     } catch (...) {
@@ -538,9 +591,10 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
         set_error("host allocation of the staging matrix failed");
         return H2_ERR_ALLOC;
     }
+    }
     const CplxIn srcZ{data->Z, data->dtype}, srcU{data->U, data->dtype}, srcW{data->W, data->dtype},
         srcT{data->T, data->dtype}, srcS{data->S, data->dtype};
-    bool finite = true;
+    if (!on_device)
     for (auto &ph : phases) {
         const int64_t np = (int64_t)ph.size();
 #pragma omp parallel for schedule(dynamic, 4) reduction(&& : finite)
@@ -598,10 +652,58 @@ h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2
     S.leaf_elems = leaf_elems;
     S.max_rank = max_rank;
     h->mat_elems = mat_elems;
-    st = upload_and_finish(h, device, hmat.data(), std::move(htasks), std::move(hsegs), counts);
+    st = upload_and_finish(h, device, on_device ? nullptr : hmat.data(), std::move(htasks), std::move(hsegs), counts);
     if (st != H2_OK) return st;
+    if (on_device) {
+        DeviceGuard dev_guard(device);
+        DevPiece *d_pieces = nullptr;
+        int *d_bad = nullptr;
+        int bad = 0;
+        cudaError_t e = dev_guard.err;
+        const size_t npc = dpieces.size();
+        if (e == cudaSuccess) e = cudaMemset(h->d_mat, 0, (size_t)std::max<int64_t>(h->mat_elems, 32) * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+        // pieces in chunks, so that the descriptor buffer stays small
+        const size_t chunk = 1u << 20;
+        if (e == cudaSuccess && npc) e = cudaMalloc(&d_pieces, std::min(npc, chunk) * sizeof(DevPiece));
+        for (size_t p0 = 0; e == cudaSuccess && p0 < npc; p0 += chunk) {
+            const size_t cnt = std::min(chunk, npc - p0);
+            e = cudaMemcpy(d_pieces, dpieces.data() + p0, cnt * sizeof(DevPiece), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) {
+                dev_pack_kernel<<<(unsigned)cnt, 256>>>(d_pieces, h->d_mat, d_bad);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+        if (d_pieces) cudaFree(d_pieces);
+        if (d_bad) cudaFree(d_bad);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error(std::string("h2_load_device: packing failed: ") + cudaGetErrorString(e));
+            h2_free(h);
+            return e == cudaErrorMemoryAllocation ? H2_ERR_ALLOC : H2_ERR_CUDA;
+        }
+        if (bad) {
+            h2_free(h);
+            return arg_error("data: non-finite entry");
+        }
+    }
     *out = h;
     return H2_OK;
+}
+
+extern "C" {
+
+h2_status h2_load(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out)
+{
+    return load_impl(tree, data, opts, out, false);
+}
+
+h2_status h2_load_device(const h2_tree *tree, const h2_data *data, const char *opts, h2_handle **out)
+{
+    return load_impl(tree, data, opts, out, true);
 }
 
 h2_status h2_device_status(h2_handle *h)

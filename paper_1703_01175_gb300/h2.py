@@ -84,6 +84,9 @@ def lib() -> ctypes.CDLL:
     L.h2_load.restype = ctypes.c_int
     L.h2_load.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Data), ctypes.c_char_p,
                           ctypes.POINTER(ctypes.c_void_p)]
+    L.h2_load_device.restype = ctypes.c_int
+    L.h2_load_device.argtypes = [ctypes.POINTER(_Tree), ctypes.POINTER(_Data), ctypes.c_char_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
     L.h2_free.restype = None
     L.h2_free.argtypes = [ctypes.c_void_p]
     L.h2_matvec.restype = ctypes.c_int
@@ -139,7 +142,7 @@ def _check(status: int, where: str):
 
 def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
-    return ["h2_load", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats", "h2_sym_near", "h2_sym_near_stats",
+    return ["h2_load", "h2_load_device", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats", "h2_sym_near", "h2_sym_near_stats",
             "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_autotune",
             "h2_status_string", "h2_last_error"]
 
@@ -263,6 +266,46 @@ class H2Matrix:
         self._h = h
         self.device = device
         self._keep = None  # the library copied everything
+
+    @classmethod
+    def from_device(cls, dh, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,
+                    wait_limit: int | None = None, sym_couple: bool = False) -> "H2Matrix":
+        """Load H^2 arrays whose blocks are complex64 tensors on `device` (a
+        construct_gpu.DeviceH2) through h2_load_device: the blocks are packed
+        on the device and never copied to the host."""
+        import torch
+        for name in ("U", "W", "T", "S", "Z"):
+            a = getattr(dh, name)
+            if a is None:
+                continue
+            if not (a.is_cuda and a.dtype == torch.complex64 and a.device.index == device):
+                raise TypeError(f"{name} must be a complex64 tensor on cuda:{device}")
+        arrs = dh
+        tr = _Tree(arrs.n, arrs.nc, len(arrs.level_ptr) - 1, _ip(arrs.level_ptr, _i32p),
+                   _ip(arrs.child, _i32p), _ip(arrs.begin, _i32p), _ip(arrs.size, _i32p),
+                   _ip(arrs.rank, _i32p))
+        d = _Data(H2_C64,
+                  arrs.U.data_ptr(), _ip(arrs.U_off, _i64p), arrs.U.numel(),
+                  arrs.W.data_ptr() if arrs.W is not None else None, _ip(arrs.W_off, _i64p),
+                  arrs.W.numel() if arrs.W is not None else 0,
+                  arrs.T.data_ptr(), _ip(arrs.T_off, _i64p), arrs.T.numel(),
+                  _ip(arrs.adm_ptr, _i32p), _ip(arrs.adm_col, _i32p),
+                  arrs.S.data_ptr(), _ip(arrs.S_off, _i64p), arrs.S.numel(),
+                  _ip(arrs.near_ptr, _i32p), _ip(arrs.near_col, _i32p),
+                  arrs.Z.data_ptr(), _ip(arrs.Z_off, _i64p), arrs.Z.numel())
+        opts = f"device={device};graphs={int(graphs)};tc_pipeline={int(tc_pipeline)};sym_couple={int(sym_couple)}"
+        if wait_limit is not None:
+            opts += f";wait_limit={int(wait_limit)}"
+        torch.cuda.synchronize(device)
+        h = ctypes.c_void_p()
+        _check(lib().h2_load_device(ctypes.byref(tr), ctypes.byref(d), opts.encode(), ctypes.byref(h)),
+               "h2_load_device")
+        self = cls.__new__(cls)
+        self._h = h
+        self.device = device
+        self._keep = None
+        self.n = arrs.n
+        return self
 
     @classmethod
     def from_file(cls, path: str, device: int = 0, graphs: bool = True, tc_pipeline: bool = True,

@@ -112,3 +112,14 @@ def test_load_file_rejects_foreign_and_corrupted_files(tmp_path):
     assert b"truncated or corrupted" in L.h2_last_error()
     with pytest.raises(h2py.H2Error):
         h2py.H2Matrix.from_file(str(junk))
+
+
+def test_constructor_library_exports_every_declared_symbol():
+    """libh2con.so (the GPU constructor kernels) loads on a host without a GPU
+    and exports every function include/h2con.h declares."""
+    from paper_1703_01175_gb300 import construct_gpu
+    L = construct_gpu.lib()
+    names = _declared("h2con.h")
+    assert "h2c_aca" in names and "h2c_gemm_grouped" in names
+    for name in names:
+        assert hasattr(L, name), name

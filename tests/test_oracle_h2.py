@@ -159,3 +159,25 @@ def test_pairwise_symmetry_of_stored_blocks(case, request):
             assert np.abs(hZ.Z[(s, t)] - partner).max() <= 1e-12 * np.abs(Z).max()
             n_near += 1
     assert n_near > 0
+
+
+@pytest.mark.parametrize("case", ["cube8", "ragged"])
+def test_row_product_equals_full_product(case, request):
+    """oracle.h2rows evaluates rows of the H^2 product from the flat C-ABI
+    arrays (Eqs. 8-9 written out per row); on these operators every row must
+    equal the full product h2mv.h2_matvec, for one and for several columns,
+    and with the flat arrays stored in complex64 (the rounded data)."""
+    from oracle import h2rows
+    from paper_1703_01175_gb300 import h2 as h2py
+    Kt, tr, pa, hK, hZ, Zt = request.getfixturevalue(case)
+    for dtype in (np.complex128, np.complex64):
+        flat = h2py.arrays_from_blocks(tr.n, tr.level_ptr, tr.child, tr.begin, tr.size, hZ.rank,
+                                       hZ.U, hZ.W, hZ.T, hZ.S, hZ.Z, dtype=dtype)
+        X = synth.random_complex(tr.n, 3, cols=3)
+        rows = np.arange(tr.n)
+        Y = h2rows.matvec_rows(flat, X, rows)
+        ref = np.stack([h2mv.h2_matvec(hZ, X[:, j]) for j in range(3)], axis=1)
+        tol = 1e-12 if dtype == np.complex128 else 1e-6
+        assert np.linalg.norm(Y - ref) <= tol * np.linalg.norm(ref)
+        y1 = h2rows.matvec_rows(flat, X[:, 1], rows[::7])
+        assert np.allclose(y1, Y[::7, 1], rtol=0, atol=1e-13 * np.abs(Y).max())

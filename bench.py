@@ -127,6 +127,20 @@ def build_workload(name: str):
     return w, arrs, perm, time.time() - t0
 
 
+def build_workload_gpu(name: str, device: int):
+    """H^2 data of the workload built on the GPU (setup; the same algorithm as
+    the host constructor). Returns (workload, host copy of the arrays, tree
+    permutation, seconds, DeviceH2 for h2_load_device)."""
+    import synth
+    from paper_1703_01175_gb300 import construct_gpu
+    w = synth.workload(name)
+    v = w.voxels
+    t0 = time.time()
+    dh = construct_gpu.build_vie_h2_gpu(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps, device=device)
+    arrs = dh.to_host()
+    return w, arrs, dh.perm, time.time() - t0, dh
+
+
 def _traffic_from_profile(kernel_src: str, which: str):
     """Per-launch DRAM traffic of the near-field or coupling launch on the
     32^3 cube from the committed ncu summary, if it was taken on the current
@@ -158,8 +172,7 @@ def oracle_matvec_fn(arrs, perm):
 def _blas_threads():
     try:
         from paper_1703_01175_gb300.construct import _BlasThreads
-        fs, fg = _BlasThreads._lookup()
-        return fg() if fg is not None else os.cpu_count()
+        return _BlasThreads.threads()
     except Exception:
         return os.cpu_count()
 
@@ -197,8 +210,10 @@ def run_ours(args, rank, world, local_rank):
     build.build_all()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w, arrs, perm, t_build = build_workload(args.workload)
-    A = h2py.H2Matrix(arrs, device=local_rank)
+    w, arrs, perm, t_build, dh = build_workload_gpu(args.workload, local_rank)
+    A = h2py.H2Matrix.from_device(dh, device=local_rank)
+    dh.free()
+    del dh
     n = arrs.n
     if args.only_mrhs:
         # profiling mode: the multi-RHS product alone (no autotuner trial
@@ -405,6 +420,7 @@ def run_ours(args, rank, world, local_rank):
         mr = {"nrhs": R}
         entries = st["near_elems"] + st["coupling_elems"] + 2 * st["transfer_elems"] + 2 * st["leaf_elems"]
         tc_entries = st["near_elems"] + st["coupling_elems"]
+        tc_tuning = A.autotune(nrhs_tc=R, fp32=False)
         for label, prec in (("splitbf16", "splitbf16"), ("fp32", "fp32")):
             for _ in range(3):
                 A.matvec(Xm, Ym, prec=prec)
@@ -422,6 +438,24 @@ def run_ours(args, rank, world, local_rank):
         # executed on the tensor cores: 3 split products per real MAC (padding not counted)
         mr["splitbf16"]["tensor_tflops_executed"] = 3.0 * mr["splitbf16"]["algorithmic_tflops"]
         mr["splitbf16"]["tensor_frac_of_bf16_peak"] = mr["splitbf16"]["tensor_tflops_executed"] * 1e3 / _peaks_bf16()
+        # streamed: hi and lo bf16 of Re and Im of every stored entry (8 B), X read and Y written once
+        split_bytes = 8.0 * entries + 16.0 * R * n
+        mr["splitbf16"]["bytes"] = split_bytes
+        mr["splitbf16"]["gbs"] = split_bytes / (mr["splitbf16"]["ms"] * 1e-3) / 1e9
+        mr["splitbf16"]["frac_hbm"] = mr["splitbf16"]["gbs"] / _peaks()[0]
+        mr["splitbf16"]["pipeline_depths"] = {k: v["ns"] for k, v in tc_tuning.items()}
+        # the same product launched directly, without the captured graph
+        A.configure(graphs=False)
+        for _ in range(3):
+            A.matvec(Xm, Ym, prec="splitbf16")
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            A.matvec(Xm, Ym, prec="splitbf16")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        A.configure(graphs=True)
+        mr["splitbf16"]["ms_without_graph"] = e0.elapsed_time(e1) / args.steps
         mr["status"] = A.device_status()
         mr["speedup_vs_single_rhs_fp32"] = (ms * R) / mr["splitbf16"]["ms"]
         mr["tc_entries"] = tc_entries
@@ -470,6 +504,7 @@ def run_ours(args, rank, world, local_rank):
                              "arnoldi": NEW_ARNOLDI}
         # plain batched: the same right-hand sides in lockstep, FP32 CUDA-core products, FP64 Arnoldi at the
         # default eta, FP64-accumulated restart residuals -- isolates what mixed precision buys
+    if args.gmres_batch > 0 and args.plain_batched:
         torch.cuda.synchronize(dev)
         g0.record(stream)
         Xp, info_p = A.gmres_batched(Bt, tol=w.tol, restart=m_new, maxit=4000, refine=True, prec="fp32",
@@ -486,9 +521,10 @@ def run_ours(args, rank, world, local_rank):
                                "products": "FP32 CUDA-core multi-RHS GEMMs; FP64 Gram-Schmidt; "
                                            "FP64-accumulated restart residuals"}
         del Xp
+        gm["new_vs_plain_batched_per_rhs"] = gm["plain_batched"]["ms_per_rhs"] / gm["new_batched"]["ms_per_rhs"]
+    if args.gmres_batch > 0:
         gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
         gm["new_vs_plain_df_per_rhs"] = gm["plain_m%d_df" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
-        gm["new_vs_plain_batched_per_rhs"] = gm["plain_batched"]["ms_per_rhs"] / gm["new_batched"]["ms_per_rhs"]
 
     # learned preconditioner (shipped weights, trained by train_precond on the 16^3 cube): flexible
     # GMRES(50) with M(v) = v + N(v) against plain GMRES(50), on the bench cube and on the training cube
@@ -565,7 +601,7 @@ def run_ours(args, rank, world, local_rank):
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload, "l2": "H^2 data per step larger than L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}", "h2_build_s": round(t_build, 1),
+                   "parallelism": f"replicas x{world}", "h2_build_s": round(t_build, 1), "h2_built_on": "GPU (construct_gpu)",
                    "h2_bytes_per_step": total_bytes, "near_blocks": st["near_blocks"],
                    "adm_blocks": st["adm_blocks"], "max_rank": st["max_rank"]},
         "matvec_gbs": mv_gbs, "matvec_frac_hbm": mv_gbs / hbm,
@@ -588,6 +624,94 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
     }
+    print(json.dumps(line), flush=True)
+
+
+def run_geometry(args, local_rank):
+    """One of the paper's scaling geometries at full size (BASELINE configs 3
+    and 5): H^2 data built on the GPU (construct_gpu, timed separately), loaded
+    through h2_load_device; the FP32 single-RHS product and the split-bf16
+    product of the workload's right-hand sides, each with its algorithmic bytes
+    against the HBM peak; ranks and admissible blocks per level; bytes per
+    unknown."""
+    import torch
+    import synth
+    from paper_1703_01175_gb300 import build, construct_gpu, h2 as h2py
+    build.build_all()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload(args.geometry)
+    v = w.voxels
+    t0 = time.time()
+    dh = construct_gpu.build_vie_h2_gpu(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps,
+                                        device=local_rank)
+    torch.cuda.synchronize(dev)
+    t_build = time.time() - t0
+    build_info = dh.info
+    rank, lp = dh.rank.astype(np.int64), dh.level_ptr
+    adm_rows = np.diff(dh.adm_ptr.astype(np.int64))
+    levels = []
+    for l in range(len(lp) - 1):
+        r = rank[lp[l]:lp[l + 1]]
+        a = adm_rows[lp[l]:lp[l + 1]]
+        if r.max() == 0 and a.sum() == 0:
+            continue
+        levels.append({"level": l, "clusters": int(len(r)), "n_t": int(dh.size[lp[l]]), "max_rank": int(r.max()),
+                       "mean_rank": round(float(r.mean()), 1), "adm_blocks": int(a.sum()),
+                       "C_sp": round(float(a.sum()) / max(1, int((a > 0).sum())), 1)})
+    t1 = time.time()
+    A = h2py.H2Matrix.from_device(dh, device=local_rank)
+    t_load = time.time() - t1
+    dh.free()
+    del dh
+    torch.cuda.empty_cache()
+    st = A.stats()
+    n = st["n"]
+    entries = st["near_elems"] + st["coupling_elems"] + 2 * st["transfer_elems"] + 2 * st["leaf_elems"]
+    hbm, peak_kind = _peaks()
+    x = torch.from_numpy(synth.random_complex(n, 1).astype(np.complex64)).to(dev)
+    y = torch.empty_like(x)
+    A.autotune()
+    for _ in range(max(3, args.warmup)):
+        A.matvec(x, y)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        e0.record()
+        for _ in range(args.steps):
+            A.matvec(x, y)
+        e1.record()
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    bytes_fp32 = 8.0 * entries + 16.0 * n
+    R = w.nrhs
+    Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
+    Xm = Xm.to(dev).t().contiguous().t()
+    Ym = torch.empty_like(Xm)
+    for _ in range(3):
+        A.matvec(Xm, Ym, prec="splitbf16")
+    torch.cuda.synchronize(dev)
+    e0.record()
+    for _ in range(args.steps):
+        A.matvec(Xm, Ym, prec="splitbf16")
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_split = e0.elapsed_time(e1) / args.steps
+    status = A.device_status()
+    A.close()
+    bytes_split = 8.0 * entries + 2 * 8.0 * R * n   # hi and lo bf16 of Re and Im per stored entry; X read, Y written
+    tensor_tflops = 24.0 * R * entries / (ms_split * 1e-3) / 1e12   # executed: 3 split products x 4 real MACs x 2
+    line = {"geometry": args.geometry, "n": n, "nrhs": R, "h2_build_s": round(t_build, 1),
+            "h2_build_stages_s": {k: round(v, 2) for k, v in build_info["seconds"].items()},
+            "load_s": round(t_load, 2),
+            "fp32": {"ms": ms, "gbs": bytes_fp32 / (ms * 1e-3) / 1e9, "frac_hbm": bytes_fp32 / (ms * 1e-3) / 1e9 / hbm,
+                     "bytes": bytes_fp32},
+            "splitbf16": {"ms": ms_split, "us_per_rhs": 1e3 * ms_split / R, "gbs": bytes_split / (ms_split * 1e-3) / 1e9,
+                          "frac_hbm": bytes_split / (ms_split * 1e-3) / 1e9 / hbm, "tensor_tflops_executed": tensor_tflops,
+                          "tensor_frac_of_bf16_peak": tensor_tflops * 1e3 / _peaks_bf16(), "status": status},
+            "bytes_per_unknown": bytes_fp32 / n, "stored_entries": entries, "max_rank": st["max_rank"],
+            "near_blocks": st["near_blocks"], "adm_blocks": st["adm_blocks"], "levels": levels,
+            "peak_gbs": hbm, "peak_source": peak_kind, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -643,11 +767,18 @@ def main():
     ap.add_argument("--gmres-steps", type=int, default=60, help="Arnoldi steps of the --only-gmres cycle")
     ap.add_argument("--arnoldi", default="fp32", choices=["fp64", "df", "fp32"],
                     help="Arnoldi arithmetic of the --only-gmres cycle")
+    ap.add_argument("--geometry", default=None, choices=["slab256", "cube64v", "array4096", "cube48"],
+                    help="time one full-size scaling geometry built on the GPU and exit")
+    ap.add_argument("--no-plain-batched", dest="plain_batched", action="store_false",
+                    help="skip the batched plain GMRES arm (FP64 Arnoldi, about two minutes)")
     ap.add_argument("--only-matvec", action="store_true",
                     help="time the products only (no GMRES, host-pointer or CPU legs): a fixed launch sequence")
     args = ap.parse_args()
     if args.fp_rates:
         fp_rates()
+        return
+    if args.geometry:
+        run_geometry(args, int(os.environ.get("LOCAL_RANK", "0")))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -112,9 +112,10 @@ typedef struct {
  * failure *out is set to NULL and nothing is leaked.
  * `opts` may be NULL or a string of "key=value" pairs separated by ';':
  * "device=<int>" (default 0), "graphs=0|1" (default 1: the single-RHS FP32
- * product is captured into a CUDA graph per (x, y) pair on first use and
- * replayed afterwards; at most 8 graphs are kept, least recently used first
- * out), "tc_pipeline=0|1" (default 1: the split-bf16 tensor-core kernel runs
+ * product is captured into a CUDA graph per (x, y) pair, and the split-bf16
+ * product per (x, y, leading dimension, nrhs), on first use and replayed
+ * afterwards; at most 8 graphs of each kind are kept, least recently used
+ * first out), "tc_pipeline=0|1" (default 1: the split-bf16 tensor-core kernel runs
  * the deepest pipeline that fits in shared memory, up to 6 stages; 0: two),
  * "wait_limit=N" (polls of every bounded wait inside the tensor-core kernels,
  * default 2^24; when one runs out the kernel waits for its copies and MMAs in
@@ -202,6 +203,38 @@ h2_status h2_device_status(h2_handle *h);
  * when report is not NULL. Synchronous; drops cached graphs.
  */
 h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len);
+
+/*
+ * Autotune the split-bf16 tensor-core product for nrhs right-hand sides: for
+ * every phase (leaf forward transforms, upward transfers per level, merged
+ * coupling / downward tiles per level, merged near-field / leaf-expansion
+ * tiles) time each pipeline depth that fits in shared memory (2 ... 6
+ * stages) with CUDA events and keep the fastest. Writes a JSON report
+ * ("tc_<phase>": {"ns": depth, "us": time, "tiles": count, "tried": {...}})
+ * into report[0..report_len) when report is not NULL. Allocates the
+ * tensor-core state and planes for nrhs if needed; synchronous; drops
+ * captured graphs. The paper has no counterpart (launch-shape tuning).
+ */
+h2_status h2_autotune_tc(h2_handle *h, int32_t nrhs, char *report, int32_t report_len);
+
+/*
+ * Apply a report of h2_autotune or h2_autotune_tc (for instance one cached
+ * from an earlier run on the same GPU and operator shape) without timing
+ * anything: "<phase>": {"threads": N} sets a CTA size (a multiple of 32 in
+ * [rows / 2, 1024]), "<phase>": {"ns": N} a tensor-core pipeline depth
+ * (0 ... 6; 0 = deepest that fits). H2_ERR_ARG for an unknown phase or a bad
+ * value. Drops captured graphs.
+ */
+h2_status h2_apply_tuning(h2_handle *h, const char *report);
+
+/*
+ * Change options of a loaded handle: "graphs=0|1" (capture the single-RHS
+ * FP32 product and the split-bf16 product into CUDA graphs keyed by their
+ * arguments and replay them; both are rebuilt on next use) and
+ * "tc_pipeline=0|1" (as in h2_load). H2_ERR_ARG when no known option is
+ * given.
+ */
+h2_status h2_configure(h2_handle *h, const char *opts);
 
 /* Sizes of the loaded representation (all counts in complex elements). */
 typedef struct {

@@ -72,52 +72,63 @@ def _i64p(a):
 
 
 class _BlasThreads:
-    """Context manager pinning numpy's OpenBLAS to n threads (no-op when the
-    thread-control symbol cannot be found), so that a pool of Python worker
-    threads does not oversubscribe the cores."""
-    _fns = None
+    """Context manager pinning every loaded OpenBLAS (numpy and scipy each
+    bring their own) to n threads (no-op for a library whose thread-control
+    symbol cannot be found), so that a pool of Python worker threads does not
+    oversubscribe the cores."""
+    _cache = {}   # library path -> (set, get) or None
 
     def __init__(self, n):
         self.n = n
-        self.old = None
+        self.old = []
 
     @classmethod
     def _lookup(cls):
-        if cls._fns is not None:
-            return cls._fns
-        cls._fns = (None, None)
+        """(set, get) function pairs of every OpenBLAS mapped into the process."""
         try:
-            libs = set()
             with open("/proc/self/maps") as f:
-                for line in f:
-                    if "openblas" in line and line.strip().endswith(".so") or ".so." in line and "openblas" in line:
-                        libs.add(line.split()[-1])
-            for path in libs:
-                L = ctypes.CDLL(path)
+                libs = sorted({line.split()[-1] for line in f
+                               if "openblas" in line and (line.strip().endswith(".so") or ".so." in line)})
+        except OSError:
+            libs = []
+        out = []
+        for path in libs:
+            if path not in cls._cache:
+                cls._cache[path] = None
+                try:
+                    L = ctypes.CDLL(path)
+                except OSError:
+                    continue
                 for sset, sget in (("scipy_openblas_set_num_threads64_", "scipy_openblas_get_num_threads64_"),
+                                   ("scipy_openblas_set_num_threads", "scipy_openblas_get_num_threads"),
                                    ("openblas_set_num_threads64_", "openblas_get_num_threads64_"),
                                    ("openblas_set_num_threads", "openblas_get_num_threads")):
                     if hasattr(L, sset) and hasattr(L, sget):
                         fs, fg = getattr(L, sset), getattr(L, sget)
                         fs.argtypes, fs.restype = [ctypes.c_int], None
                         fg.argtypes, fg.restype = [], ctypes.c_int
-                        cls._fns = (fs, fg)
-                        return cls._fns
-        except OSError:
-            pass
-        return cls._fns
+                        cls._cache[path] = (fs, fg)
+                        break
+            if cls._cache[path] is not None:
+                out.append(cls._cache[path])
+        return out
+
+    @classmethod
+    def threads(cls) -> int:
+        """Threads of the first pinned library (os.cpu_count() if none is found)."""
+        fns = cls._lookup()
+        return fns[0][1]() if fns else (os.cpu_count() or 1)
 
     def __enter__(self):
-        fs, fg = self._lookup()
-        if fs is not None:
-            self.old = fg()
+        self.old = []
+        for fs, fg in self._lookup():
+            self.old.append((fs, fg()))
             fs(self.n)
         return self
 
     def __exit__(self, *exc):
-        fs, _ = self._lookup()
-        if fs is not None and self.old is not None:
-            fs(self.old)
+        for fs, n in self.old:
+            fs(n)
 
 TWO_PI = 2.0 * math.pi
 

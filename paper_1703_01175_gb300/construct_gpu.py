@@ -37,7 +37,6 @@ import time
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
-import scipy.linalg
 
 from . import construct
 from .construct import TWO_PI, _BlasThreads
@@ -185,6 +184,29 @@ class _Gpu:
                                        self.stream), "h2c_gemm_grouped")
         self._keep = (dd, dp, di)
 
+    def gemm_np(self, A, B, C, m, n, k, opa, opb, beta, lda, ldb, ldc, alpha=1.0, out_f64=False):
+        """Grouped products from arrays (scalars broadcast), like gemm()."""
+        cnt_ = np.broadcast(A, B, C, m, n, k, lda, ldb, ldc).shape
+        nprob = cnt_[0] if cnt_ else 1
+        d = np.zeros(nprob, dtype=GEMM_DESC)
+        for f, v in (("A", A), ("B", B), ("C", C), ("m", m), ("n", n), ("k", k), ("opa", opa), ("opb", opb),
+                     ("beta", beta), ("lda", lda), ("ldb", ldb), ("ldc", ldc)):
+            d[f] = v
+        d["alpha_re"], d["alpha_im"] = complex(alpha).real, complex(alpha).imag
+        d = d[(d["m"] > 0) & (d["n"] > 0)]
+        if len(d) == 0:
+            return
+        tm = (d["m"].astype(np.int64) + 63) // 64
+        tn = (d["n"].astype(np.int64) + 63) // 64
+        cnt = tm * tn
+        prob = np.repeat(np.arange(len(d), dtype=np.int32), cnt)
+        start = np.repeat(np.cumsum(cnt) - cnt, cnt)
+        idx = (np.arange(int(cnt.sum()), dtype=np.int64) - start).astype(np.int32)
+        dd, dp, di = self.up(d), self.up(prob), self.up(idx)
+        _check(self.L.h2c_gemm_grouped(dd.data_ptr(), dp.data_ptr(), di.data_ptr(), len(prob), int(out_f64),
+                                       self.stream), "h2c_gemm_grouped")
+        self._keep = (dd, dp, di)
+
     def sync(self):
         self.torch.cuda.synchronize(self.dev)
 
@@ -193,16 +215,31 @@ def _ptr(t, elem_off=0, elem_bytes=8):
     return int(t.data_ptr()) + int(elem_off) * elem_bytes
 
 
-def _trunc_eig(G: np.ndarray, eps: float) -> np.ndarray:
-    """Eigenvectors of the Hermitian PSD G with eigenvalue > eps^2 lambda_max
-    (Eqs. 11, 15), in decreasing order."""
-    G = 0.5 * (G + G.conj().T)
-    w, Q = np.linalg.eigh(G)
-    w, Q = w[::-1], Q[:, ::-1]
-    if w.size == 0 or w[0] <= 0.0:
-        return Q[:, :0]
-    kk = int(np.count_nonzero(w > eps * eps * w[0]))
-    return np.ascontiguousarray(Q[:, :kk])
+def _trunc_eig_many(items, eps, pool, threads):
+    """_trunc_eig for many Hermitian matrices: items is a list of (key, G);
+    matrices of one size are stacked and decomposed in chunks across the host
+    threads. Returns {key: eigenvectors with eigenvalue > eps^2 lambda_max}."""
+    by_n = {}
+    for key, G in items:
+        by_n.setdefault(G.shape[0], []).append((key, G))
+    chunks = []
+    for n_, lst in by_n.items():
+        step = max(4, -(-len(lst) // threads))
+        chunks += [lst[c:c + step] for c in range(0, len(lst), step)]
+
+    def run(lst):
+        St = np.stack([G for _, G in lst])
+        St = 0.5 * (St + np.conj(np.swapaxes(St, 1, 2)))
+        w, Q = np.linalg.eigh(St)
+        out = []
+        for b, (key, _) in enumerate(lst):
+            wb, Qb = w[b, ::-1], Q[b, :, ::-1]
+            kk = 0 if wb.size == 0 or wb[0] <= 0.0 else int(np.count_nonzero(wb > eps * eps * wb[0]))
+            out.append((key, np.ascontiguousarray(Qb[:, :kk])))
+        return out
+
+    with _BlasThreads(1):
+        return dict(r for part in pool.map(run, chunks) for r in part)
 
 
 def _reduced_svd_from_grams(Gu, Gv, eps):
@@ -240,6 +277,68 @@ def _reduced_svd_from_grams(Gu, Gv, eps):
     return Wu, C
 
 
+def _reduced_svd_stack(Gu, Gv, Lm, k, eps):
+    """Eq. 7 for a stack of cross approximations padded to one size K.
+
+    Gu, Gv: (B, K, K) Gram matrices U^H U and V^H V of the factors (the first
+    k[b] rows and columns used); Lm: (B, K, K) lower-triangular pivot matrices
+    (L_ll = pivot, L_lp = U[I_l, p]) of the cross approximations. With the
+    Cholesky factors of the column-normalised Gram matrices, U = Q_U R_U and
+    V = Q_V R_V (R = L^H diag(column norms)); the singular values and left
+    vectors of M = R_U R_V^T come from the Hermitian eigenproblem of M M^H in
+    FP64 (singular values above eps sigma_1, a relative threshold well inside
+    FP64's range), and Y = M^H X Sigma^{-1}. Returns per b: W_u = R_U^{-1} X
+    Sigma (A = U W_u) and D = L^{-T} R_V^{-1} conj(Y) (B_t = G^t[I, :]^T D),
+    both k[b] x kk[b], or None for a matrix whose Cholesky factorisation fails
+    (the caller then takes the eigen-decomposition route)."""
+    B, K = Gu.shape[0], Gu.shape[1]
+    pad = np.arange(K)[None, :] >= np.asarray(k)[:, None]          # (B, K): padded columns
+    eye = np.eye(K)
+
+    def factor(G):
+        d = np.sqrt(np.maximum(np.real(np.diagonal(G, axis1=1, axis2=2)), 0.0))
+        d = np.where(pad | (d <= 0.0), 1.0, d)
+        Gh = G / d[:, :, None] / d[:, None, :]
+        Gh = np.where(pad[:, :, None] | pad[:, None, :], 0.0, Gh) + pad[:, :, None] * eye[None]
+        Gh = 0.5 * (Gh + np.conj(np.swapaxes(Gh, 1, 2)))
+        ok = np.ones(B, dtype=bool)
+        L = np.zeros_like(Gh)
+        try:
+            L = np.linalg.cholesky(Gh)
+        except np.linalg.LinAlgError:
+            for b in range(B):
+                try:
+                    L[b] = np.linalg.cholesky(Gh[b])
+                except np.linalg.LinAlgError:
+                    ok[b] = False
+                    L[b] = eye
+        R = np.conj(np.swapaxes(L, 1, 2)) * d[:, None, :]                 # upper triangular, identity padding
+        return R, ok
+
+    Ru, oku = factor(Gu)
+    Rv, okv = factor(Gv)
+    keep = ~pad
+    Rum = Ru * keep[:, :, None]
+    Rvm = Rv * keep[:, :, None]
+    M = Rum @ np.swapaxes(Rvm, 1, 2)
+    w, X = np.linalg.eigh(M @ np.conj(np.swapaxes(M, 1, 2)))
+    w, X = w[:, ::-1], X[:, :, ::-1]
+    sig = np.sqrt(np.maximum(w, 0.0))
+    kk = np.array([int(np.count_nonzero(sig[b] > eps * sig[b, 0])) if sig[b, 0] > 0 else 0 for b in range(B)])
+    inv = np.where(np.arange(K)[None, :] < kk[:, None], 1.0 / np.where(sig > 0, sig, 1.0), 0.0)
+    Y = (np.conj(np.swapaxes(M, 1, 2)) @ X) * inv[:, None, :]
+    Wu = np.linalg.solve(Ru, X * sig[:, None, :])
+    C = np.linalg.solve(Rv, np.conj(Y))
+    D = np.linalg.solve(np.swapaxes(Lm, 1, 2), C)
+    out = []
+    for b in range(B):
+        if not (oku[b] and okv[b]):
+            out.append(None)
+        else:
+            out.append((Wu[b, :k[b], :kk[b]], D[b, :k[b], :kk[b]]))
+    return out
+
+
 def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, eps_aca=None,
                      eps_stage1=None, device=0, batch_bytes=None, threads=None, verbose=False) -> DeviceH2:
     """Build the H^2 arrays of Z = I - K diag(chi) for voxels at `centres` on
@@ -255,7 +354,7 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
     eps_stage1 = eps / 3.0 if eps_stage1 is None else eps_stage1
     if batch_bytes is None:
         free, total = torch.cuda.mem_get_info(g.dev)
-        batch_bytes = int(min(32e9, 0.25 * free))
+        batch_bytes = int(min(96e9, 0.4 * free))
     centres = np.ascontiguousarray(centres, dtype=np.float64)
     chi_vox = np.asarray(eps_r, dtype=np.complex128) - 1.0
     a_eq = (3.0 * float(dv) / (4.0 * math.pi)) ** (1.0 / 3.0)
@@ -313,6 +412,7 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
         by_level.setdefault(int(lev[t]), []).append(t)
     prev_max = 0
     pool = ThreadPoolExecutor(threads)
+    tsub = {"aca_kernel": 0.0, "grams": 0.0, "host_svd": 0.0, "factor_gemm": 0.0, "prep": 0.0}
     for L_ in sorted(by_level, reverse=True):
         queue = []
         for t in by_level[L_]:
@@ -347,6 +447,7 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
                 vo += cap * ncols
                 qo += m
                 po += cap
+            tq = time.time()
             dcol = g.up(np.concatenate(colv))
             djobs = g.up(jobs)
             U = g.empty_c64(uo)
@@ -356,10 +457,15 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
             pval = g.empty_c64(po)
             kout = torch.empty(nj, dtype=torch.int32, device=g.dev)
             stat = torch.empty(nj, dtype=torch.int32, device=g.dev)
+            g.sync()
+            tsub["prep"] += time.time() - tq
+            tq = time.time()
             _check(g.L.h2c_aca(cen.data_ptr(), vie, dcol.data_ptr(), djobs.data_ptr(), nj, float(eps_aca),
                                U.data_ptr(), V.data_ptr(), used.data_ptr(), prow.data_ptr(), pval.data_ptr(),
                                kout.data_ptr(), stat.data_ptr(), g.stream), "h2c_aca")
             kk_h = kout.cpu().numpy()
+            tsub["aca_kernel"] += time.time() - tq
+            tq = time.time()
             st_h = stat.cpu().numpy()
             done = []
             for i, (t, m, ncols, cap) in enumerate(batch):
@@ -399,25 +505,57 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
             Upiv = (U[torch.from_numpy(np.concatenate(gidx)).to(g.dev)].cpu().numpy() if gidx
                     else np.zeros(0, np.complex64))
             G_h = G.cpu().numpy()
+            tsub["grams"] += time.time() - tq
+            tq = time.time()
 
-            def host_job(i):
-                t, m, ncols, cap = batch[i]
+            # the reduced SVDs, stacked by padded size and split across host threads
+            groups = {}
+            for i in done:
                 kp = int(kk_h[i])
-                if kp == 0:
-                    return i, np.zeros((0, 0)), np.zeros((0, 0)), np.zeros(0, np.int64)
-                o = goff[i]
-                Gu = G_h[o:o + kp * kp].reshape(kp, kp, order="F").astype(np.complex128)
-                Gv = G_h[o + kp * kp:o + 2 * kp * kp].reshape(kp, kp, order="F").astype(np.complex128)
-                Wu, C = _reduced_svd_from_grams(Gu, Gv, eps_stage1)
-                up = Upiv[gpos[i]:gpos[i] + kp * kp].reshape(kp, kp).astype(np.complex128)
-                pv = pval_h[jobs[i]["piv_off"]:jobs[i]["piv_off"] + kp].astype(np.complex128)
-                Lm = np.tril(up, -1) + np.diag(pv)
-                D = scipy.linalg.solve_triangular(Lm.T, C, lower=False) if C.shape[1] else C
-                pr = prow_h[jobs[i]["piv_off"]:jobs[i]["piv_off"] + kp].astype(np.int64)
-                return i, Wu, D, pr
+                if kp > 0:
+                    groups.setdefault((kp + 7) // 8 * 8, []).append(i)
+            chunks = []
+            for K_, idxs in groups.items():
+                step = max(8, -(-len(idxs) // threads))
+                chunks += [(K_, idxs[c:c + step]) for c in range(0, len(idxs), step)]
+
+            def host_chunk(arg):
+                K_, idxs = arg
+                nb = len(idxs)
+                Gu = np.zeros((nb, K_, K_), dtype=np.complex128)
+                Gv = np.zeros((nb, K_, K_), dtype=np.complex128)
+                Lm = np.tile(np.eye(K_, dtype=np.complex128), (nb, 1, 1))
+                ks = np.zeros(nb, dtype=np.int64)
+                prs = []
+                for b_, i in enumerate(idxs):
+                    kp = int(kk_h[i])
+                    ks[b_] = kp
+                    o = goff[i]
+                    Gu[b_, :kp, :kp] = G_h[o:o + kp * kp].reshape(kp, kp, order="F")
+                    Gv[b_, :kp, :kp] = G_h[o + kp * kp:o + 2 * kp * kp].reshape(kp, kp, order="F")
+                    up = Upiv[gpos[i]:gpos[i] + kp * kp].reshape(kp, kp)
+                    pv = pval_h[jobs[i]["piv_off"]:jobs[i]["piv_off"] + kp]
+                    Lm[b_, :kp, :kp] = np.tril(up, -1) + np.diag(pv)
+                    prs.append(prow_h[jobs[i]["piv_off"]:jobs[i]["piv_off"] + kp].astype(np.int64))
+                out = _reduced_svd_stack(Gu, Gv, Lm, ks, eps_stage1)
+                res_ = []
+                for b_, i in enumerate(idxs):
+                    kp = int(ks[b_])
+                    if out[b_] is None:   # Cholesky failed: eigen-decomposition route
+                        Wu, C = _reduced_svd_from_grams(Gu[b_, :kp, :kp], Gv[b_, :kp, :kp], eps_stage1)
+                        D = np.linalg.solve(Lm[b_, :kp, :kp].T, C) if C.shape[1] else C
+                    else:
+                        Wu, D = out[b_]
+                    res_.append((i, Wu, D, prs[b_]))
+                return res_
 
             with _BlasThreads(1):
-                res = list(pool.map(host_job, done))
+                res = [r for part in pool.map(host_chunk, chunks) for r in part]
+            for i in done:
+                if int(kk_h[i]) == 0:
+                    s1rank[batch[i][0]] = (0, 0)
+            tsub["host_svd"] += time.time() - tq
+            tq = time.time()
             # A_t = U W_u, stored (kk x m) column-major, i.e. row-major m x kk
             rows = []
             for i, Wu, D, pr in res:
@@ -436,14 +574,19 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
                 fac[t] = {"A": A, "kk": kk, "kp": kp, "piv": piv_u, "D": D, "Wd": Wd}
             g.gemm(rows)
             g.sync()
+            tsub["factor_gemm"] += time.time() - tq
             for t in fac:
                 fac[t].pop("Wd", None)
             del U, V, used, prow, pval, G, dcol, djobs
+            if verbose:
+                print(f"construct_gpu:   batch of {nj} jobs (level {L_}), {used_b / 1e9:.1f} GB of factors, "
+                      f"max rank {int(kk_h.max()) if nj else 0}; cumulative {tsub}", flush=True)
         prev_max = max(prev_max, level_max)
         if verbose:
             print(f"construct_gpu: stage I level {L_}: {len(by_level[L_])} clusters, max ACA rank {level_max}",
                   flush=True)
     secs["stage1"] = time.time() - t0
+    secs.update({"stage1_" + k_: v_ for k_, v_ in tsub.items()})
 
     # ---- Stage II: bases and transfers, bottom-up ------------------------------------
     t0 = time.time()
@@ -500,12 +643,9 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
             G2h = G2.cpu().numpy()
             del G2
 
-            def leaf_basis(t):
-                o = goff[t]
-                return t, _trunc_eig(G2h[o:o + nt[t] ** 2].reshape(nt[t], nt[t], order="F"), eps)
-
-            with _BlasThreads(1):
-                res = list(pool.map(leaf_basis, leaves))
+            bases = _trunc_eig_many([(t, G2h[goff[t]:goff[t] + nt[t] ** 2].reshape(nt[t], nt[t], order="F"))
+                                     for t in leaves], eps, pool, threads)
+            res = [(t, bases[t]) for t in leaves]
             rows = []
             for t, Vt in res:
                 rank[t] = Vt.shape[1]
@@ -556,14 +696,10 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
             G2h = G2.cpu().numpy()
             del G2
 
-            def inner_basis(w):
-                t, c1, c2, k1, k2 = w
-                d = k1 + k2
-                o = goff[t]
-                return w, _trunc_eig(G2h[o:o + d * d].reshape(d, d, order="F"), eps)
-
-            with _BlasThreads(1):
-                res = list(pool.map(inner_basis, work))
+            bases = _trunc_eig_many([(w_[0], G2h[goff[w_[0]]:goff[w_[0]] + (w_[3] + w_[4]) ** 2]
+                                      .reshape(w_[3] + w_[4], w_[3] + w_[4], order="F")) for w_ in work],
+                                    eps, pool, threads)
+            res = [(w_, bases[w_[0]]) for w_ in work]
             rows1, rows2 = [], []
             for (t, c1, c2, k1, k2), Pm in res:
                 kt = Pm.shape[1]
@@ -625,6 +761,14 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
     g.sync()
     for t in fac:
         fac[t].pop("Dd", None)
+    kp_of = np.zeros(nc, dtype=np.int64)
+    piv_ptr = np.zeros(nc, dtype=np.uint64)
+    F_ptr = np.zeros(nc, dtype=np.uint64)
+    for t in fac:
+        kp_of[t] = fac[t]["kp"]
+        piv_ptr[t] = fac[t]["piv"].data_ptr()
+    for t, X_ in F.items():
+        F_ptr[t] = X_.data_ptr()
     pairs_by_level = {}
     for j in range(len(adm)):
         t, s = int(adm_t[j]), int(adm_s[j])
@@ -655,24 +799,26 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
                 rows.append((_ptr(cur_below[c2]), _ptr(Pm_dev[c], k1), _ptr(X, n1), n2, kc, k2, H2C_N, H2C_N, 0, n2,
                              ld, n1 + n2, 1.0))
         g.gemm(rows)
-        plist = pairs_by_level.get(L_, [])
+        plist = np.asarray(pairs_by_level.get(L_, []), dtype=np.int64)
+        cur_ptr = np.zeros(nc, dtype=np.uint64)
+        for c_, X_ in cur.items():
+            cur_ptr[c_] = X_.data_ptr()
         # batches of pairs whose products Q fit in batch_bytes
-        qsz = np.array([int(rank[adm_s[j]]) * fac[int(adm_t[j])]["kp"] for j in plist], dtype=np.int64)
+        qsz = rank[adm_s[plist]] * kp_of[adm_t[plist]] if len(plist) else np.zeros(0, dtype=np.int64)
+        cum = np.cumsum(8 * qsz)
         i0 = 0
         while i0 < len(plist):
-            i1, acc = i0, 0
-            while i1 < len(plist) and (i1 == i0 or acc + 8 * qsz[i1] <= batch_bytes):
-                acc += 8 * qsz[i1]
-                i1 += 1
+            base = int(cum[i0 - 1]) if i0 else 0
+            i1 = max(i0 + 1, int(np.searchsorted(cum, base + batch_bytes, side="right")))
             sel = plist[i0:i1]
-            qoff = np.concatenate([[0], np.cumsum(qsz[i0:i1])[:-1]])
+            ts_, ss_ = adm_t[sel], adm_s[sel]
+            qoff = np.concatenate([[0], np.cumsum(qsz[i0:i1])[:-1]]).astype(np.int64)
             Q = g.empty_c64(int(qsz[i0:i1].sum()))
             cd = np.zeros(len(sel), dtype=COUPLE_DESC)
-            for q, j in enumerate(sel):
-                t, s = int(adm_t[j]), int(adm_s[j])
-                ks = int(rank[s])
-                cd[q] = (_ptr(cur[s]), _ptr(fac[t]["piv"], 0, 4), _ptr(Q, qoff[q]), 3 * int(vs[s]), ks,
-                         int(vb[s]), int(vs[s]), ks, fac[t]["kp"])
+            cd["Vs"], cd["piv"] = cur_ptr[ss_], piv_ptr[ts_]
+            cd["Q"] = np.uint64(Q.data_ptr()) + (8 * qoff).astype(np.uint64)
+            cd["ldv"], cd["ldq"] = 3 * vs[ss_], rank[ss_]
+            cd["s_v0"], cd["s_nv"], cd["ks"], cd["kp"] = vb[ss_], vs[ss_], rank[ss_], kp_of[ts_]
             tm = (cd["ks"].astype(np.int64) + 63) // 64
             tn = (cd["kp"].astype(np.int64) + 63) // 64
             cnt = tm * tn
@@ -683,24 +829,21 @@ def build_vie_h2_gpu(centres, dv, eps_r, n_min=96, eta=1.0, eps=1e-4, k=TWO_PI, 
             _check(g.L.h2c_couple_grouped(cen.data_ptr(), vie, dcd.data_ptr(), dp.data_ptr(), di.data_ptr(),
                                           len(prob), g.stream), "h2c_couple_grouped")
             # S^{t,s} = -F_t Q^T (the system matrix carries -K)
-            rows = []
-            for q, j in enumerate(sel):
-                t, s = int(adm_t[j]), int(adm_s[j])
-                kt, ks, kp = int(rank[t]), int(rank[s]), fac[t]["kp"]
-                rows.append((_ptr(F[t]), _ptr(Q, qoff[q]), _ptr(S, S_off[j]), kt, ks, kp, H2C_N, H2C_T, 0, kt,
-                             ks, kt, -1.0))
-            g.gemm(rows)
+            g.gemm_np(F_ptr[ts_], cd["Q"], np.uint64(S.data_ptr()) + (8 * S_off[sel]).astype(np.uint64),
+                      rank[ts_], rank[ss_], kp_of[ts_], H2C_N, H2C_T, 0, rank[ts_], rank[ss_], rank[ts_], alpha=-1.0)
             g.sync()
             del Q, dcd, dp, di
             i0 = i1
         cur_below = cur
     del cur_below, F, PT
     # S^{s,t} = (S^{t,s})^T exactly: the mean of the two skeleton estimates
-    key = {(int(adm_t[j]), int(adm_s[j])): j for j in range(len(adm))}
-    sel = [(j, key[(int(adm_s[j]), int(adm_t[j]))]) for j in range(len(adm))
-           if adm_t[j] < adm_s[j] and ssz[j] > 0]
-    if sel:
-        a = np.array(sel, dtype=np.int64)
+    keys = adm_t * nc + adm_s                       # increasing: the pairs are sorted
+    j_ts = np.nonzero((adm_t < adm_s) & (ssz > 0))[0]
+    j_st = np.searchsorted(keys, adm_s[j_ts] * nc + adm_t[j_ts])
+    assert np.array_equal(keys[j_st], adm_s[j_ts] * nc + adm_t[j_ts]), "partition is not symmetric"
+    if len(j_ts):
+        a = np.stack([j_ts, j_st], axis=1).astype(np.int64)
+        sel = a
         d_ts, d_st = g.up(S_off[a[:, 0]]), g.up(S_off[a[:, 1]])
         d_kt = g.up(rank[adm_t[a[:, 0]]].astype(np.int32))
         d_ks = g.up(rank[adm_s[a[:, 0]]].astype(np.int32))

@@ -17,6 +17,7 @@
 #include <new>
 #include <string>
 #include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include "h2_internal.h"
@@ -247,6 +248,7 @@ void h2_free(h2_handle *h)
     cudaFree(h->d_ybuf);
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    h2_drop_split_graphs(h);
     if (h->s_cap) cudaStreamDestroy(h->s_cap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_near) cudaEventDestroy(h->ev_near);
@@ -1043,6 +1045,47 @@ static void drop_graphs(h2_handle *h)
 {
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    h2_drop_split_graphs(h);
+}
+
+// The split-bf16 product of nrhs columns captured into a CUDA graph per
+// (x, y, ld, nrhs) on first use and replayed afterwards (at most 8 kept, least
+// recently used out); the tensor-core state and planes are allocated before
+// any capture, and graphs are dropped whenever the planes move.
+static h2_status run_split_graph(h2_handle *h, const float2 *x, float2 *y, int64_t ld, int nrhs, cudaStream_t st)
+{
+    int moved = 0;
+    h2_status s = h2_split_prepare(h, nrhs, &moved);
+    if (s != H2_OK) return s;
+    if (moved) h2_drop_split_graphs(h);
+    for (auto &g : h->split_graphs)
+        if (g.x == x && g.y == y && g.ld == ld && g.nrhs == nrhs) {
+            g.last_use = ++h->graph_clock;
+            H2_CUDA(cudaGraphLaunch(g.exec, st));
+            return H2_OK;
+        }
+    cudaGraph_t graph = nullptr;
+    H2_CUDA(cudaStreamBeginCapture(h->s_cap, cudaStreamCaptureModeThreadLocal));
+    s = h2_run_multi_split(h, x, ld, y, ld, nrhs, h->s_cap);
+    const cudaError_t ec = cudaStreamEndCapture(h->s_cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t ei = cudaErrorUnknown;
+    if (s == H2_OK && ec == cudaSuccess && graph) ei = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        h->use_graphs = false;  // capture unsupported here: direct launches from now on
+        return h2_run_multi_split(h, x, ld, y, ld, nrhs, st);
+    }
+    if (h->split_graphs.size() >= 8) {
+        auto victim = std::min_element(h->split_graphs.begin(), h->split_graphs.end(),
+                                       [](const auto &a, const auto &b) { return a.last_use < b.last_use; });
+        cudaGraphExecDestroy(victim->exec);
+        h->split_graphs.erase(victim);
+    }
+    h->split_graphs.push_back({x, y, ld, nrhs, exec, ++h->graph_clock});
+    H2_CUDA(cudaGraphLaunch(exec, st));
+    return H2_OK;
 }
 
 extern "C" {
@@ -1104,9 +1147,13 @@ h2_status h2_matvec(h2_handle *h, const void *x, void *y, int32_t nrhs, int64_t 
     DeviceGuard dev_guard(h->device);
     H2_CUDA(dev_guard.err);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (prec == H2_PREC_SPLITBF16)
-        return h2_run_multi_split(h, reinterpret_cast<const float2 *>(x), nrhs > 1 ? ld : h->n,
-                                  reinterpret_cast<float2 *>(y), nrhs > 1 ? ld : h->n, nrhs, st);
+    if (prec == H2_PREC_SPLITBF16) {
+        const int64_t ldd = nrhs > 1 ? ld : h->n;
+        if (h->use_graphs)
+            return run_split_graph(h, reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), ldd, nrhs, st);
+        return h2_run_multi_split(h, reinterpret_cast<const float2 *>(x), ldd, reinterpret_cast<float2 *>(y), ldd,
+                                  nrhs, st);
+    }
     if (nrhs > 1 && prec == H2_PREC_FP32)
         return h2_run_multi_f32(h, reinterpret_cast<const float2 *>(x), ld, reinterpret_cast<float2 *>(y), ld, nrhs, st);
     if (nrhs == 1 && prec == H2_PREC_FP32 && h->sym_couple && !h->sym) {
@@ -1306,4 +1353,95 @@ extern "C" h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len)
         report[report_len - 1] = 0;
     }
     return s;
+}
+
+extern "C" h2_status h2_autotune_tc(h2_handle *h, int32_t nrhs, char *report, int32_t report_len)
+{
+    if (!h) return arg_error("h2_autotune_tc: NULL handle");
+    if (nrhs < 1) return arg_error("h2_autotune_tc: nrhs must be >= 1");
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
+    std::string js = "{";
+    bool first = true;
+    const h2_status s = h2_split_autotune(h, nrhs, js, first);
+    js += "}";
+    if (report && report_len > 0) {
+        strncpy(report, js.c_str(), (size_t)report_len - 1);
+        report[report_len - 1] = 0;
+    }
+    return s;
+}
+
+// Entries of a tuning report: "<phase>": {"threads": N ...} (CTA size of an FP32
+// phase) or "<phase>": {"ns": N ...} (pipeline depth of a tensor-core phase).
+extern "C" h2_status h2_apply_tuning(h2_handle *h, const char *report)
+{
+    if (!h || !report) return arg_error("h2_apply_tuning: NULL argument");
+    std::unordered_map<std::string, Phase *> fp;
+    fp["near"] = &h->near;
+    fp["couple"] = &h->couple;
+    fp["upleaf"] = &h->upleaf;
+    fp["leafexp"] = &h->leafexp;
+    for (int l = 0; l < h->nlev; ++l) {
+        fp["up" + std::to_string(l)] = &h->up[l];
+        fp["down" + std::to_string(l)] = &h->down[l];
+    }
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
+    const std::string r(report);
+    bool tc_seen = false;
+    for (const char *field : {"{\"threads\": ", "{\"ns\": "}) {
+        size_t pos = 0;
+        while ((pos = r.find(field, pos)) != std::string::npos) {
+            const int val = atoi(r.c_str() + pos + strlen(field));
+            // the key: the quoted name before the ": " that precedes this object
+            const size_t q1 = r.rfind('"', pos >= 3 ? pos - 3 : 0);
+            const size_t q0 = q1 == std::string::npos || q1 == 0 ? std::string::npos : r.rfind('"', q1 - 1);
+            pos += strlen(field);
+            if (q0 == std::string::npos) return arg_error("h2_apply_tuning: malformed report");
+            const std::string key = r.substr(q0 + 1, q1 - q0 - 1);
+            if (field[2] == 't') {
+                auto it = fp.find(key);
+                if (it == fp.end()) return arg_error("h2_apply_tuning: unknown phase " + key);
+                int maxP = 1;
+                for (const Task &t : it->second->tasks) maxP = std::max(maxP, t.mpad / 2);
+                if (val < maxP || val > 1024 || val % 32) return arg_error("h2_apply_tuning: bad CTA size for " + key);
+                it->second->threads = val;
+            } else {
+                if (!tc_seen) {
+                    // the tensor-core state is built before the first depth is set
+                    const h2_status s = h2_split_prepare(h, 1, nullptr);
+                    if (s != H2_OK) return s;
+                    tc_seen = true;
+                }
+                if (val < 0 || val > 6) return arg_error("h2_apply_tuning: bad pipeline depth for " + key);
+                if (!h2_split_set_ns(h, key, val)) return arg_error("h2_apply_tuning: unknown phase " + key);
+            }
+        }
+    }
+    drop_graphs(h);
+    return H2_OK;
+}
+
+extern "C" h2_status h2_configure(h2_handle *h, const char *opts)
+{
+    if (!h || !opts) return arg_error("h2_configure: NULL argument");
+    DeviceGuard dev_guard(h->device);
+    H2_CUDA(dev_guard.err);
+    const char *g = strstr(opts, "graphs=");
+    const char *tp = strstr(opts, "tc_pipeline=");
+    if (!g && !tp) return arg_error("h2_configure: no known option");
+    if (g) {
+        h->use_graphs = atoi(g + 7) != 0;
+        drop_graphs(h);
+    }
+    if (tp) {
+        h->tc_pipeline = atoi(tp + 12) != 0;
+        if (h->split) {
+            const h2_status s = h2_split_set_pipeline(h, h->tc_pipeline ? 1 : 0);
+            if (s != H2_OK) return s;
+        }
+        h2_drop_split_graphs(h);
+    }
+    return H2_OK;
 }

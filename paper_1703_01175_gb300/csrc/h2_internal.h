@@ -52,14 +52,14 @@ enum PhaseKind { PH_NEAR = 0, PH_UPLEAF, PH_UP, PH_DOWN, PH_LEAFEXP, PH_COUNT };
 
 // One tile of the split-bf16 tensor-core path (h2_umma.cu): up to 128 output
 // rows of a task (or of several tasks with the same output merged along K),
-// its packed matrix images and its input chunk table.
+// its packed matrix images and its input group table.
 struct UTask {
     int32_t out_off;    // first output row: complex offset in y, or position in the bf16 plane
     int32_t m;          // complex rows in this tile (<= 128)
     int32_t n;          // real MMA N = 2 * round_up(m, 8)
     int32_t nst;        // K stages of 16 complex columns
     int64_t img_off;    // byte offset of stage 0's image (hi plane, then lo plane)
-    int32_t chunk_off;  // first entry in the chunk table (4 per stage)
+    int32_t chunk_off;  // first entry in the group table (2 plane positions per stage)
     int32_t pad_;
 };
 
@@ -71,11 +71,12 @@ struct UPackInfo {
 struct UPhase {
     int ntile = 0;
     UTask *d_tasks = nullptr;
-    int32_t *d_chunks = nullptr;
+    int32_t *d_chunks = nullptr;  // plane position of every 8-column group of every tile
     uint8_t *d_images = nullptr;
     int64_t image_bytes = 0;
     int nmax = 16;                // largest MMA N of the phase's tiles
     int maxnst = 0;               // most K stages of a tile
+    int ns = 0;                   // pipeline stages chosen by the autotuner (0: the deepest that fits)
 };
 
 struct SplitState {
@@ -85,7 +86,8 @@ struct SplitState {
     UPhase leaf, upleaf;
     std::vector<UPhase> up, level;
     // one bf16 plane: x at positions [0, np_x), xh at [np_x, np_x + np_c), yh
-    // at [np_x + np_c, np_x + 2 np_c); nch chunks per tile, the last one zero
+    // at [np_x + np_c, np_x + 2 np_c); nch groups of 8 positions per tile (a
+    // Re chunk and an Im chunk each), the last one zero
     int64_t np_x = 0, np_c = 0, nch = 0;
     int32_t *d_xpos = nullptr;    // x plane position -> index into x (-1: padding)
     void *phi = nullptr, *plo = nullptr;
@@ -241,6 +243,16 @@ struct h2_handle {
         uint64_t last_use;
     };
     std::vector<GraphEntry> graphs;
+    // captured split-bf16 products, one per (x, y, leading dimension, nrhs)
+    struct SplitGraphEntry {
+        const void *x;
+        void *y;
+        int64_t ld;
+        int32_t nrhs;
+        cudaGraphExec_t exec;
+        uint64_t last_use;
+    };
+    std::vector<SplitGraphEntry> split_graphs;
     uint64_t graph_clock = 0;
     bool use_graphs = true;
     bool tc_pipeline = true;          // split-bf16: deepest tensor-core pipeline that fits (else two stages)
@@ -272,6 +284,15 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
                              cudaStream_t st);
 h2_status h2_split_error_flag(h2_handle *h, int *flag);
 h2_status h2_split_set_pipeline(h2_handle *h, int on);
+// allocate the tensor-core state and planes for nrhs right-hand sides (never
+// during a stream capture); *realloc = 1 when the planes moved
+h2_status h2_split_prepare(h2_handle *h, int nrhs, int *realloc);
+// time every pipeline depth of every tensor-core phase for nrhs right-hand
+// sides and keep the fastest; appends "tc_<phase>": {...} entries to js
+h2_status h2_split_autotune(h2_handle *h, int nrhs, std::string &js, bool &first);
+// set the pipeline depth of a tensor-core phase by its report name; false if unknown
+bool h2_split_set_ns(h2_handle *h, const std::string &name, int ns);
+void h2_drop_split_graphs(h2_handle *h);
 void h2_free_precond(h2_handle *h);
 void h2_free_bkrylov(h2_handle *h);
 void h2_free_bicgstab(h2_handle *h);

@@ -1,28 +1,34 @@
 // Multi-RHS H2 product on the 5th-generation tensor cores (tcgen05), with
 // operands split into two bf16 terms and FP32 accumulation in tensor memory.
 //
-// For R right-hand sides a task out (m x R) = M (m x ncol) X (ncol x R) is the
-// real GEMM  D (R x 2m) = Xr (R x 2 ncol) . A2 (2m x 2 ncol)^T  with
-//   Xr[r][2c + 0/1] = Re/Im x_r(c)  and, per complex entry a = M[i][c],
-//   A2[2i][2c] = Re a, A2[2i][2c+1] = -Im a, A2[2i+1][2c] = Im a, A2[2i+1][2c+1] = Re a,
-// so that D[r][2i], D[r][2i+1] are the real and imaginary parts of y_r(i).
-// Each operand is split as v = hi + lo (bf16) and D accumulates hi.hi, hi.lo and
-// lo.hi (the lo.lo term is below the FP32 rounding of the result).
+// For R right-hand sides a task out (m x R) = M (m x ncol) X (ncol x R) is
+// formed from two real GEMMs that share one matrix operand:
+//   P (R x 2m) = Xre (R x ncol) . B (2m x ncol)^T,
+//   Q (R x 2m) = Xim (R x ncol) . B (2m x ncol)^T,
+// where B holds each complex entry a = M[i][c] once: row "re i" = Re a, row
+// "im i" = Im a, in groups of 8 output rows (8 re rows, then the 8 im rows).
+// Then y_r(i) = (P[r][re i] - Q[r][im i]) + j (P[r][im i] + Q[r][re i]):
+// the complex product needs no real expansion of the matrix, which is stored
+// and streamed at 8 bytes per complex entry (hi and lo bf16 of Re and Im).
+// Each operand is split as v = hi + lo (bf16); P and Q accumulate hi.hi,
+// hi.lo and lo.hi (the lo.lo term is below the FP32 rounding of the result).
 //
-// Tiles: M = 128 right-hand sides (one tile of TMEM lanes), N = 2 m rounded up
-// to 16 (<= 256), K staged 32 bf16 (16 complex columns) at a time in the
-// no-swizzle K-major shared-memory layout. The matrix operand is pre-packed
-// once on the device into that exact shared-memory image and fetched with one
-// bulk asynchronous copy per stage. The right-hand-side operand lives in one
-// pair of bf16 planes (hi, lo) stored chunk-major: a chunk is 4 complex
-// entries (16 bytes) of all 128 right-hand sides of a tile, 2 KB contiguous,
-// and every input segment starts on a chunk boundary, so a stage's operand is
-// 4 bulk copies per plane. The planes hold x, the coefficients xh of the
-// upward pass and yh of the downward pass; every transform writes its output
-// split straight into them (thread = right-hand side = one 16-byte chunk row),
-// so the tree passes never round-trip through FP32 buffers. The couplings of
-// a cluster and its downward transfer share one tile (their columns
-// concatenated along K), as do the near field and the leaf expansion of a leaf.
+// Tiles: M = 128 right-hand sides (one tile of TMEM lanes), N = 2 m rounded
+// up to 16 (<= 256), K staged 16 complex columns (one MMA K step) at a time
+// in the no-swizzle K-major shared-memory layout. The matrix operand is
+// pre-packed once on the device into that exact shared-memory image and
+// fetched with one bulk asynchronous copy per stage. The right-hand-side
+// operand lives in one pair of bf16 planes (hi, lo) stored group-major: a
+// group is 8 complex entries of all 128 right-hand sides of a tile, as a
+// 2 KB chunk of their real parts followed by a 2 KB chunk of their imaginary
+// parts, and every input segment starts on a group boundary, so a stage's
+// operand is one or two bulk copies per plane. The planes hold x, the
+// coefficients xh of the upward pass and yh of the downward pass; every
+// transform writes its output split straight into them (thread = right-hand
+// side = one 16-byte chunk row per part), so the tree passes never
+// round-trip through FP32 buffers. The couplings of a cluster and its
+// downward transfer share one tile (their columns concatenated along K), as
+// do the near field and the leaf expansion of a leaf.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -38,11 +44,12 @@ namespace h2 {
 namespace {
 
 constexpr int UT = 128;               // threads per CTA (4 warps)
-constexpr int KST = 32;               // bf16 K elements per stage
-constexpr int CPS = KST / 2;          // complex columns per stage
-constexpr int NCH = KST / 8;          // 16-byte K chunks per stage
+constexpr int CPS = 16;               // complex columns per stage (one MMA K step of 16)
+constexpr int GRP = 8;                // complex entries per plane group (one 16-byte chunk row per part)
 constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
-constexpr int XPLANE = NCH * MT * 16; // bytes of one X plane image per stage
+constexpr int CHUNK = MT * 16;        // bytes of one chunk (16 bytes of each of 128 right-hand sides)
+constexpr int GBYTES = 2 * CHUNK;     // bytes of one group of one plane: Re chunk, then Im chunk
+constexpr int XPLANE = (CPS / GRP) * GBYTES;  // bytes of one plane's right-hand-side operand per stage
 constexpr uint32_t kDrainLimit = 1u << 22;  // waits for copies and MMAs in flight after an abort
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -100,22 +107,6 @@ __device__ __forceinline__ uint64_t bdesc(uint32_t saddr, int n)
     return d;                                         // layout type 0: no swizzle
 }
 
-// shared-memory matrix descriptor: K-major, no swizzle, 128 rows of 16-byte
-// chunks: 8-row core matrices 128 B apart (stride), chunks 2 KB apart (leading)
-__device__ __forceinline__ uint64_t xdesc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
-    d |= (uint64_t)(2048 >> 4) << 16;                 // leading byte offset: next chunk along K
-    d |= (uint64_t)(128 >> 4) << 32;                  // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
-    return d;                                         // layout type 0: no swizzle
-}
-
-// byte offset of chunk c (4 complex entries) of right-hand-side tile t in a
-// chunk-major plane with nchp chunks per tile (the last one all zero)
-__device__ __forceinline__ int64_t plane_chunk(int t, int64_t nchp, int c) { return ((int64_t)t * nchp + c) * (MT * 16); }
-
 // instruction descriptor: bf16 x bf16 -> f32, both K-major, M = 128, N = n
 __device__ __forceinline__ uint32_t idesc_bf16(int n)
 {
@@ -138,21 +129,48 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar)
                  : "memory");
 }
 
+// shared-memory matrix descriptor of the right-hand-side operand: K-major, no
+// swizzle, 128 rows of 16-byte chunks: 8-row core matrices 128 B apart
+// (stride), consecutive K chunks one plane group (4 KB) apart (leading)
+__device__ __forceinline__ uint64_t xdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
+    d |= (uint64_t)(GBYTES >> 4) << 16;               // leading byte offset: next chunk along K
+    d |= (uint64_t)(128 >> 4) << 32;                  // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
+    return d;                                         // layout type 0: no swizzle
+}
+
+// byte offset of group g (8 complex entries) of right-hand-side tile t in a
+// group-major plane with ngrp groups per tile (the last one all zero)
+__device__ __forceinline__ int64_t plane_group(int t, int64_t ngrp, int64_t g) { return ((int64_t)t * ngrp + g) * GBYTES; }
+
+__device__ __forceinline__ void split_bf16x8(const float *v, __nv_bfloat16 *hv, __nv_bfloat16 *lv)
+{
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        hv[e] = __float2bfloat16_rn(v[e]);
+        lv[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hv[e]));
+    }
+}
+
 }  // namespace
 
 // One tile of a split-bf16 task (see h2_internal.h: UTask), NS-stage pipelined. Thread 0
 // produces: for each K stage it waits until the buffer is free (tcgen05.commit
 // of the MMAs that read it) and issues the bulk copies of the matrix image and
-// of the 16 right-hand-side chunks, which complete on the stage's `full`
-// barrier (expect_tx); a missing chunk reads the plane's zero chunk. Lane 0 of
-// warp 3 issues the MMAs of a stage once it is full and commits them to the
-// stage's `empty` barrier. All four warps then read the accumulator out of
-// tensor memory. Both operands use the no-swizzle K-major layout: right-hand
-// sides as whole 2 KB chunks, the matrix image as NCH chunks of N rows.
+// of the stage's two right-hand-side groups (merged into one copy per plane
+// when they are adjacent), which complete on the stage's `full` barrier
+// (expect_tx); a missing group reads the plane's zero group. Lane 0 of warp 3
+// issues the MMAs of a stage once it is full (three split products into P from
+// the real parts, three into Q from the imaginary parts) and commits them to
+// the stage's `empty` barrier. All four warps then read both accumulators out
+// of tensor memory and combine them.
 template <int NS>
 __global__ void __launch_bounds__(UT, 1)
-umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chunks,
-               const uint8_t *__restrict__ images, __nv_bfloat16 *phi, __nv_bfloat16 *plo, int64_t nchp,
+umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ groups,
+               const uint8_t *__restrict__ images, __nv_bfloat16 *phi, __nv_bfloat16 *plo, int64_t ngrp,
                int nrhs, float2 *__restrict__ out, int64_t ldo, int nmax, uint32_t tcols, int *__restrict__ err,
                uint32_t wait_limit)
 {
@@ -160,8 +178,9 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const UTask tk = tasks[blockIdx.x];
     const int N = tk.n;
-    const uint32_t abytes = (uint32_t)N * 16u * NCH;       // one plane of the matrix image per stage
-    const uint32_t astride = 2u * (uint32_t)nmax * 16u * NCH;
+    const uint32_t abytes = (uint32_t)N * 16u * (CPS / 8);  // one plane of the matrix image per stage
+    const uint32_t astride = 2u * (uint32_t)nmax * 16u * (CPS / 8);
+    const uint32_t qcol = tcols >> 1;                      // Q accumulator: second half of the columns
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
     uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
@@ -193,17 +212,17 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        // producer: per stage one bulk copy of the matrix image and 2 NCH bulk
-        // copies of right-hand-side chunks (NCH per plane), all completing on
-        // the stage's `full` barrier; chunk indices are read a stage ahead
+        // producer: per stage one bulk copy of the matrix image and one or two
+        // bulk copies per plane of right-hand-side groups, all completing on
+        // the stage's `full` barrier; group indices are read a stage ahead
         const uint8_t *ph = reinterpret_cast<const uint8_t *>(phi), *pl = reinterpret_cast<const uint8_t *>(plo);
-        static_assert(NCH == 4, "one int4 of chunk indices per stage");
-        const int4 *cq = reinterpret_cast<const int4 *>(chunks + tk.chunk_off);
-        int4 c0 = tk.nst > 0 ? cq[0] : make_int4(-1, -1, -1, -1);
+        static_assert(CPS / GRP == 2, "one int2 of group positions per stage");
+        const int2 *gq = reinterpret_cast<const int2 *>(groups + tk.chunk_off);
+        int2 g0 = tk.nst > 0 ? gq[0] : make_int2(-1, -1);
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
-            const int ci[NCH] = {c0.x, c0.y, c0.z, c0.w};
-            if (s + 1 < tk.nst) c0 = cq[s + 1];
+            const int64_t ga = g0.x >= 0 ? g0.x / GRP : ngrp - 1, gb = g0.y >= 0 ? g0.y / GRP : ngrp - 1;
+            if (s + 1 < tk.nst) g0 = gq[s + 1];
             if (s >= NS && !mbar_wait(&empty[b], ((s / NS) - 1) & 1, wait_limit)) {
                 abort_flag = 1;
                 break;
@@ -213,15 +232,20 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             uint8_t *sa = sab + b * astride;
             mbar_expect_tx(&full[b], 2 * abytes + 2 * XPLANE);
             bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
-#pragma unroll
-            for (int q = 0; q < NCH; ++q) {
-                const int64_t off = plane_chunk(blockIdx.y, nchp, ci[q] >= 0 ? ci[q] >> 2 : (int)nchp - 1);
-                bulk_g2s(sx + q * 2048, ph + off, 2048, &full[b]);
-                bulk_g2s(sx + XPLANE + q * 2048, pl + off, 2048, &full[b]);
+            const int64_t oa = plane_group(blockIdx.y, ngrp, ga), ob = plane_group(blockIdx.y, ngrp, gb);
+            if (gb == ga + 1) {
+                bulk_g2s(sx, ph + oa, 2 * GBYTES, &full[b]);
+                bulk_g2s(sx + XPLANE, pl + oa, 2 * GBYTES, &full[b]);
+            } else {
+                bulk_g2s(sx, ph + oa, GBYTES, &full[b]);
+                bulk_g2s(sx + GBYTES, ph + ob, GBYTES, &full[b]);
+                bulk_g2s(sx + XPLANE, pl + oa, GBYTES, &full[b]);
+                bulk_g2s(sx + XPLANE + GBYTES, pl + ob, GBYTES, &full[b]);
             }
         }
     } else if (warp == 3 && lane == 0) {
         const uint32_t idesc = idesc_bf16(N);
+        const uint32_t tq = tmem + qcol;
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
             if (!mbar_wait(&full[b], (s / NS) & 1, wait_limit)) {
@@ -230,16 +254,15 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
             }
             consumed = s + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;
+            const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;   // hi, lo planes (Re at +0, Im at +2 KB)
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
-#pragma unroll
-            for (int k = 0; k < KST / 16; ++k) {
-                const uint32_t xo = k * 2 * 2048, bo = k * 2 * 16 * (uint32_t)N;   // two chunks per K step
-                const uint32_t first = (s == 0 && k == 0) ? 0u : 1u;
-                umma(tmem, xdesc(xa + xo), bdesc(aa + bo, N), idesc, first);   // hi . hi
-                umma(tmem, xdesc(xa + xo), bdesc(ab + bo, N), idesc, 1u);      // hi . lo
-                umma(tmem, xdesc(xb + xo), bdesc(aa + bo, N), idesc, 1u);      // lo . hi
-            }
+            const uint32_t first = s == 0 ? 0u : 1u;
+            umma(tmem, xdesc(xa), bdesc(aa, N), idesc, first);                 // P: Re hi . hi
+            umma(tmem, xdesc(xa), bdesc(ab, N), idesc, 1u);                    // P: Re hi . lo
+            umma(tmem, xdesc(xb), bdesc(aa, N), idesc, 1u);                    // P: Re lo . hi
+            umma(tq, xdesc(xa + CHUNK), bdesc(aa, N), idesc, first);           // Q: Im hi . hi
+            umma(tq, xdesc(xa + CHUNK), bdesc(ab, N), idesc, 1u);              // Q: Im hi . lo
+            umma(tq, xdesc(xb + CHUNK), bdesc(aa, N), idesc, 1u);              // Q: Im lo . hi
             umma_commit(&empty[b]);
         }
     }
@@ -259,48 +282,54 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!abort_flag && tk.nst > 0) {
-        // thread = right-hand side r (TMEM lane); accumulator columns 2i, 2i + 1
-        // = Re, Im of output row i
+        // thread = right-hand side r (TMEM lane); per group of 8 output rows,
+        // accumulator columns 16 g + e hold the Re rows and 16 g + 8 + e the Im
+        // rows of B, in P (real parts of x) and Q (imaginary parts of x)
         const int rr = warp * 32 + lane, r = r0 + rr;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int j0 = 0; j0 < N; j0 += 16) {
-            uint32_t v[16];
+        for (int g = 0; g < N / 16; ++g) {
+            uint32_t pv[16], qv[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                 "[%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15])
-                : "r"(tl + (uint32_t)j0));
+                : "=r"(pv[0]), "=r"(pv[1]), "=r"(pv[2]), "=r"(pv[3]), "=r"(pv[4]), "=r"(pv[5]), "=r"(pv[6]),
+                  "=r"(pv[7]), "=r"(pv[8]), "=r"(pv[9]), "=r"(pv[10]), "=r"(pv[11]), "=r"(pv[12]), "=r"(pv[13]),
+                  "=r"(pv[14]), "=r"(pv[15])
+                : "r"(tl + (uint32_t)(16 * g)));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(qv[0]), "=r"(qv[1]), "=r"(qv[2]), "=r"(qv[3]), "=r"(qv[4]), "=r"(qv[5]), "=r"(qv[6]),
+                  "=r"(qv[7]), "=r"(qv[8]), "=r"(qv[9]), "=r"(qv[10]), "=r"(qv[11]), "=r"(qv[12]), "=r"(qv[13]),
+                  "=r"(qv[14]), "=r"(qv[15])
+                : "r"(tl + qcol + (uint32_t)(16 * g)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             if (r < nrhs) {
-                const int i0 = j0 >> 1;
+                float yre[8], yim[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    yre[e] = __uint_as_float(pv[e]) - __uint_as_float(qv[8 + e]);
+                    yim[e] = __uint_as_float(pv[8 + e]) + __uint_as_float(qv[e]);
+                }
+                const int i0 = 8 * g;
                 if (out) {
                     float2 *o = out + (int64_t)r * ldo + tk.out_off;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (i0 + q < tk.m) o[i0 + q] = make_float2(__uint_as_float(v[2 * q]), __uint_as_float(v[2 * q + 1]));
-                } else {
-                    // split into the plane: two chunks of 4 complex entries (a chunk
-                    // that starts below m may hold padding rows, whose sums are 0)
-#pragma unroll
-                    for (int hc = 0; hc < 2; ++hc) {
-                        const int ib = i0 + 4 * hc;
-                        if (ib < tk.m) {
-                            __align__(16) __nv_bfloat16 hv[8];
-                            __align__(16) __nv_bfloat16 lv[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const float f = __uint_as_float(v[8 * hc + e]);
-                                hv[e] = __float2bfloat16_rn(f);
-                                lv[e] = __float2bfloat16_rn(f - __bfloat162float(hv[e]));
-                            }
-                            const int64_t off =
-                                (((int64_t)blockIdx.y * nchp + ((tk.out_off + ib) >> 2)) * MT + rr) * 8;
-                            *reinterpret_cast<uint4 *>(phi + off) = *reinterpret_cast<const uint4 *>(hv);
-                            *reinterpret_cast<uint4 *>(plo + off) = *reinterpret_cast<const uint4 *>(lv);
-                        }
-                    }
+                    for (int e = 0; e < 8; ++e)
+                        if (i0 + e < tk.m) o[i0 + e] = make_float2(yre[e], yim[e]);
+                } else if (i0 < tk.m) {
+                    // split into the plane: the group's Re and Im chunk rows (rows
+                    // of the group at or beyond m are padding, whose sums are 0)
+                    __align__(16) __nv_bfloat16 hv[8];
+                    __align__(16) __nv_bfloat16 lv[8];
+                    const int64_t goff = plane_group(blockIdx.y, ngrp, (tk.out_off + i0) / GRP) + rr * 16;
+                    uint8_t *bh = reinterpret_cast<uint8_t *>(phi) + goff, *bl = reinterpret_cast<uint8_t *>(plo) + goff;
+                    split_bf16x8(yre, hv, lv);
+                    *reinterpret_cast<uint4 *>(bh) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(bl) = *reinterpret_cast<const uint4 *>(lv);
+                    split_bf16x8(yim, hv, lv);
+                    *reinterpret_cast<uint4 *>(bh + CHUNK) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(bl + CHUNK) = *reinterpret_cast<const uint4 *>(lv);
                 }
             }
         }
@@ -310,10 +339,15 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ chun
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
-size_t umma_ws_smem_bytes(int ns, int nmax) { return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * NCH) + 1024 + 128; }
+size_t umma_ws_smem_bytes(int ns, int nmax)
+{
+    return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * (CPS / 8)) + 1024 + 128;
+}
 
-// Pack the real-expanded, bf16-split matrix images of every tile/stage; column
-// pc of a task starts at element colmap[colmap_off + pc] of mat (-1: padding).
+// Pack the bf16-split matrix images of every tile/stage: per stage and plane,
+// two K chunks (8 complex columns each) of N rows of 16 bytes; row 16 q + e is
+// Re of task row row0 + 8 q + e and row 16 q + 8 + e its Im (e < 8). Column pc
+// of a task starts at element colmap[colmap_off + pc] of mat (-1: padding).
 __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
                                  const int64_t *__restrict__ colmap, const float2 *__restrict__ mat,
                                  uint8_t *__restrict__ images)
@@ -323,35 +357,37 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
     const int N = tk.n;
     const int s = blockIdx.y;
     if (s >= tk.nst) return;
-    uint8_t *img = images + tk.img_off + (int64_t)s * 2 * N * 16 * NCH;
-    for (int e = threadIdx.x; e < N * KST; e += blockDim.x) {
-        const int nr = e / KST, kk = e % KST;
-        const int i = pi.row0 + (nr >> 1);                 // complex row in the task matrix
-        const int pc = s * CPS + (kk >> 1);                // padded complex column
+    const int abytes = N * 16 * (CPS / 8);
+    uint8_t *img = images + tk.img_off + (int64_t)s * 2 * abytes;
+    for (int e = threadIdx.x; e < N * CPS; e += blockDim.x) {
+        const int nr = e / CPS, kk = e % CPS;
+        const int li = 8 * (nr >> 4) + (nr & 7);           // row of the tile
+        const int part = (nr >> 3) & 1;                    // 0: Re, 1: Im
+        const int pc = s * CPS + kk;                       // padded complex column
         const int64_t c = pc < pi.npc ? colmap[pi.colmap_off + pc] : -1;   // column start in mat
         float v = 0.f;
-        if (c >= 0 && (nr >> 1) < tk.m) {
-            const float2 a = mat[c + i];
-            const int part = nr & 1, comp = kk & 1;
-            v = part == 0 ? (comp == 0 ? a.x : -a.y) : (comp == 0 ? a.y : a.x);
+        if (c >= 0 && li < tk.m) {
+            const float2 a = mat[c + pi.row0 + li];
+            v = part == 0 ? a.x : a.y;
         }
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         const int byte = (kk >> 3) * (16 * N) + nr * 16 + (kk & 7) * 2;   // chunk, row, element
         *reinterpret_cast<__nv_bfloat16 *>(img + byte) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(img + N * 16 * NCH + byte) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(img + abytes + byte) = lo;
     }
 }
 
-// Fill plane positions [p0, pend) of chunk-major bf16 hi/lo planes: position
-// d of right-hand side r holds src[r * lds + pos[d]] (zero where pos[d] < 0),
-// stored in chunk d / 4 of tile r / 128, row r % 128, bytes 4 (d % 4) .. + 4
-// (Re, Im); nchp chunks per tile; p0 is a multiple of 4. A block transposes
-// 32 positions x 32 right-hand sides through shared memory, so that reads run
-// along positions and each warp writes 32 consecutive 16-byte chunk rows.
+// Fill plane positions [p0, pend) of group-major bf16 hi/lo planes: position
+// d of right-hand side r holds src[r * lds + pos[d]] (zero where pos[d] < 0);
+// its real part sits in the Re chunk of group d / 8 of tile r / 128, row
+// r % 128, bytes 2 (d % 8) .. + 2, its imaginary part in the Im chunk; ngrp
+// groups per tile; p0 is a multiple of 8. A block transposes 32 positions x 32
+// right-hand sides through shared memory, so that reads run along positions
+// and each thread writes one 16-byte chunk row (8 Re or 8 Im values) per plane.
 __global__ void __launch_bounds__(256)
 split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ pos, int p0, int pend,
-                     int nrhs, __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t nchp)
+                     int nrhs, __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t ngrp)
 {
     __shared__ float2 tile[32][33];
     const int d0 = p0 + blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -362,21 +398,21 @@ split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t 
         tile[rr][tx] = (pd >= 0 && r < nrhs) ? src[(int64_t)r * lds + pd] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int r = r0 + tx, c = (d0 >> 2) + ty;
-    if (r >= nrhs || 4 * c >= pend) return;
+    const int r = r0 + tx, gi = ty >> 1, part = ty & 1;   // 4 groups of 8 positions, Re or Im
+    const int64_t g = (d0 >> 3) + gi;
+    if (r >= nrhs || 8 * g >= pend) return;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float2 c = tile[tx][8 * gi + e];
+        v[e] = part ? c.y : c.x;
+    }
     __align__(16) __nv_bfloat16 hv[8];
     __align__(16) __nv_bfloat16 lv[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float2 v = tile[tx][4 * ty + k];
-        hv[2 * k] = __float2bfloat16_rn(v.x);
-        hv[2 * k + 1] = __float2bfloat16_rn(v.y);
-        lv[2 * k] = __float2bfloat16_rn(v.x - __bfloat162float(hv[2 * k]));
-        lv[2 * k + 1] = __float2bfloat16_rn(v.y - __bfloat162float(hv[2 * k + 1]));
-    }
-    const int64_t off = (((int64_t)(r / MT) * nchp + c) * MT + (r % MT)) * 8;
-    *reinterpret_cast<uint4 *>(phi + off) = *reinterpret_cast<const uint4 *>(hv);
-    *reinterpret_cast<uint4 *>(plo + off) = *reinterpret_cast<const uint4 *>(lv);
+    split_bf16x8(v, hv, lv);
+    const int64_t off = plane_group(r / MT, ngrp, g) + part * CHUNK + (r % MT) * 16;
+    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(phi) + off) = *reinterpret_cast<const uint4 *>(hv);
+    *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(plo) + off) = *reinterpret_cast<const uint4 *>(lv);
 }
 
 
@@ -420,23 +456,23 @@ static h2_status build_uphase(h2_handle *h, std::vector<MTask> mts, const std::v
     std::vector<int64_t> colmap;
     int64_t img = 0;
     for (const MTask &t : mts) {
-        // padded columns: each segment rounded up to a multiple of 4 complex entries
+        // padded columns: each segment rounded up to a whole plane group (8 complex entries)
         std::vector<int64_t> cm;        // padded column -> element offset of the column in mat (-1 pad)
-        std::vector<int32_t> chunk_src; // per 4-column chunk: plane position of its first entry
+        std::vector<int32_t> chunk_src; // per 8-column group: plane position of its first entry
         for (const Task *pt : t.parts) {
             int orig = 0;
             for (int si = pt->seg_begin; si < pt->seg_end; ++si) {
                 const Seg &sg = hsegs[si];
                 const int32_t pbase = seg_pos(sg);
-                const int np = (sg.n + 3) / 4 * 4;
+                const int np = (sg.n + GRP - 1) / GRP * GRP;
                 for (int j = 0; j < np; ++j) cm.push_back(j < sg.n ? pt->mat_off + (int64_t)(orig + j) * pt->mpad : -1);
-                for (int j = 0; j < np; j += 4) chunk_src.push_back(pbase + j);
+                for (int j = 0; j < np; j += GRP) chunk_src.push_back(pbase + j);
                 orig += sg.n;
             }
         }
         const int npc = (int)cm.size();
         const int nst = (npc + CPS - 1) / CPS;
-        while ((int)chunk_src.size() < nst * (CPS / 4)) chunk_src.push_back(-1);
+        while ((int)chunk_src.size() < nst * (CPS / GRP)) chunk_src.push_back(-1);
         const int64_t colmap_off = (int64_t)colmap.size();
         colmap.insert(colmap.end(), cm.begin(), cm.end());
         const int chunk_off = (int)chunks.size();
@@ -450,7 +486,7 @@ static h2_status build_uphase(h2_handle *h, std::vector<MTask> mts, const std::v
             u.nst = nst;
             u.img_off = img;
             u.chunk_off = chunk_off;
-            img += (int64_t)nst * 2 * u.n * 16 * NCH;
+            img += (int64_t)nst * 2 * u.n * 16 * (CPS / 8);
             tiles.push_back(u);
             UPackInfo pi{};
             pi.row0 = row0;
@@ -502,7 +538,7 @@ static h2_status split_init(h2_handle *h)
     S->pipeline = h->tc_pipeline;
     S->wait_limit = h->wait_limit;
     // plane layout: leaves in tree order (x), then the coefficient blocks of
-    // the clusters (xh, then yh), each block padded to 4 complex entries
+    // the clusters (xh, then yh), each block padded to a whole group of 8
     std::vector<int32_t> leaf_pbase(h->nc, -1), coef_pbase(h->nc, -1);
     int64_t p = 0;
     std::vector<int32_t> xs, xd;
@@ -513,18 +549,18 @@ static h2_status split_init(h2_handle *h)
             xs.push_back(h->begin[t] + i);
             xd.push_back((int32_t)(p + i));
         }
-        p += (h->size[t] + 3) / 4 * 4;
+        p += (h->size[t] + GRP - 1) / GRP * GRP;
     }
-    S->np_x = std::max<int64_t>(8, (p + 3) / 4 * 4);
+    S->np_x = std::max<int64_t>(GRP, p);
     int64_t q = 0;
     for (int t = 0; t < h->nc; ++t) {
         if (h->rank[t] == 0) continue;
         coef_pbase[t] = (int32_t)q;
-        q += (h->rank[t] + 3) / 4 * 4;
+        q += (h->rank[t] + GRP - 1) / GRP * GRP;
     }
-    S->np_c = std::max<int64_t>(8, (q + 3) / 4 * 4);
-    S->nch = (S->np_x + 2 * S->np_c) / 4 + 1;
-    if ((S->nch - 1) * 4 > INT32_MAX) {
+    S->np_c = std::max<int64_t>(GRP, q);
+    S->nch = (S->np_x + 2 * S->np_c) / GRP + 1;   // groups per tile, the last one all zero
+    if ((S->nch - 1) * GRP > INT32_MAX) {
         set_error("split-bf16: plane positions exceed 32 bits");
         return H2_ERR_STATE;
     }
@@ -630,14 +666,14 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
     cudaFree(S->plo);
     S->phi = S->plo = nullptr;
     S->rcap = 0;
-    // chunk-major: per tile of 128 right-hand sides, nch chunks of 2 KB
-    const size_t bytes = (size_t)rpad * S->nch * 16;
+    // group-major: per tile of 128 right-hand sides, nch groups of 4 KB (Re and Im chunks)
+    const size_t bytes = (size_t)(rpad / MT) * S->nch * GBYTES;
     if (cudaMalloc(&S->phi, bytes) != cudaSuccess || cudaMalloc(&S->plo, bytes) != cudaSuccess) {
         cudaGetLastError();
         set_error("split-bf16 plane allocation failed");
         return H2_ERR_ALLOC;
     }
-    // entries that no kernel writes stay zero: the zero chunk, padding between
+    // entries that no kernel writes stay zero: the zero group, padding between
     // blocks, and the xh / yh of clusters that no task writes
     UM_CUDA(cudaMemset(S->phi, 0, bytes));
     UM_CUDA(cudaMemset(S->plo, 0, bytes));
@@ -647,21 +683,23 @@ static h2_status ensure_planes(h2_handle *h, int rpad)
 
 // Deepest pipeline that fits in shared memory and that the phase's longest
 // tile can use (two stages when the pipeline option is off); tensor memory
-// columns: the power of two that holds the widest accumulator.
+// columns: the power of two that holds both accumulators of the widest tile.
 static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, float2 *out, int64_t ldo,
                                cudaStream_t st)
 {
     if (U.ntile == 0) return cudaSuccess;
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
     int ns = 2;
-    if (S->pipeline)
-        for (int c = std::min(6, std::max(2, U.maxnst)); c > 2; --c)
+    if (S->pipeline) {
+        const int want = U.ns > 0 ? std::min(6, U.ns) : std::min(6, std::max(2, U.maxnst));
+        for (int c = want; c > 2; --c)
             if (umma_ws_smem_bytes(c, U.nmax) <= S->dyn_smem_limit) {
                 ns = c;
                 break;
             }
+    }
     uint32_t tcols = 32;
-    while ((int)tcols < U.nmax) tcols <<= 1;
+    while ((int)tcols < 2 * U.nmax) tcols <<= 1;
     const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
     __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
 #define H2_UMMA_LAUNCH(NSV)                                                                                  \
@@ -680,6 +718,7 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
 
 void h2_free_split(h2_handle *h)
 {
+    h2_drop_split_graphs(h);
     SplitState *S = h->split;
     if (!S) return;
     std::vector<UPhase *> all = {&S->leaf, &S->upleaf};
@@ -730,6 +769,107 @@ h2_status h2_split_error_flag(h2_handle *h, int *flag)
     if (!h->split) return H2_OK;
     UM_CUDA(cudaMemcpy(flag, h->split->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     return H2_OK;
+}
+
+h2_status h2_split_prepare(h2_handle *h, int nrhs, int *realloc)
+{
+    h2_status s = split_init(h);
+    if (s != H2_OK) return s;
+    const int before = h->split->rcap;
+    s = ensure_planes(h, (nrhs + MT - 1) / MT * MT);
+    if (realloc) *realloc = h->split->rcap != before;
+    return s;
+}
+
+// the tensor-core phases with their report names
+static std::vector<std::pair<std::string, UPhase *>> split_phases(SplitState *S)
+{
+    std::vector<std::pair<std::string, UPhase *>> v = {{"tc_leaf", &S->leaf}, {"tc_upleaf", &S->upleaf}};
+    for (size_t l = 0; l < S->up.size(); ++l) v.push_back({"tc_up" + std::to_string(l), &S->up[l]});
+    for (size_t l = 0; l < S->level.size(); ++l) v.push_back({"tc_level" + std::to_string(l), &S->level[l]});
+    return v;
+}
+
+bool h2_split_set_ns(h2_handle *h, const std::string &name, int ns)
+{
+    if (!h->split) return false;
+    for (auto &pu : split_phases(h->split))
+        if (pu.first == name) {
+            pu.second->ns = ns;
+            return true;
+        }
+    return false;
+}
+
+h2_status h2_split_autotune(h2_handle *h, int nrhs, std::string &js, bool &first)
+{
+    h2_status s = h2_split_prepare(h, nrhs, nullptr);
+    if (s != H2_OK) return s;
+    SplitState *S = h->split;
+    float2 *yb = nullptr;
+    if (cudaMalloc(&yb, sizeof(float2) * (size_t)h->n * nrhs) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("h2_autotune_tc: allocation failed");
+        return H2_ERR_ALLOC;
+    }
+    cudaStream_t st = h->s_aux;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const bool pipeline = S->pipeline;
+    S->pipeline = true;
+    for (auto &pu : split_phases(S)) {
+        UPhase &U = *pu.second;
+        if (e != cudaSuccess || U.ntile == 0) continue;
+        int best = 0;
+        float best_us = 1e30f;
+        std::string tried;
+        const int old_ns = U.ns;
+        for (int c = 2; c <= 6 && e == cudaSuccess; ++c) {
+            if (umma_ws_smem_bytes(c, U.nmax) > S->dyn_smem_limit) break;
+            if (c > 2 && c > U.maxnst) break;   // deeper than the longest tile's stages buys nothing
+            U.ns = c;
+            float ts[3] = {0, 0, 0};
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = launch_umma(U, S, nrhs, &U == &S->leaf ? yb : nullptr, h->n, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ts[rep - 1] = ms;
+            }
+            std::sort(ts, ts + 3);
+            const float us = ts[1] * 1e3f;
+            tried += (tried.empty() ? "" : ", ") + std::string("\"") + std::to_string(c) + "\": " + std::to_string(us);
+            if (us < best_us) {
+                best_us = us;
+                best = c;
+            }
+        }
+        U.ns = best > 0 ? best : old_ns;
+        js += (first ? "" : ", ") + std::string("\"") + pu.first + "\": {\"ns\": " + std::to_string(U.ns) +
+              ", \"us\": " + std::to_string(best_us) + ", \"tiles\": " + std::to_string(U.ntile) +
+              ", \"tried\": {" + tried + "}}";
+        first = false;
+    }
+    S->pipeline = pipeline;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(yb);
+    h2_drop_split_graphs(h);
+    if (e != cudaSuccess) {
+        set_error(std::string("h2_autotune_tc: ") + cudaGetErrorString(e));
+        return H2_ERR_CUDA;
+    }
+    // the timing runs overwrote the planes' coefficient blocks, which every product rewrites before reading
+    return H2_OK;
+}
+
+void h2_drop_split_graphs(h2_handle *h)
+{
+    for (auto &g : h->split_graphs) cudaGraphExecDestroy(g.exec);
+    h->split_graphs.clear();
 }
 
 h2_status h2_split_set_pipeline(h2_handle *h, int on)

@@ -124,6 +124,12 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(_SolveInfo), ctypes.c_void_p]
     L.h2_autotune.restype = ctypes.c_int
     L.h2_autotune.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int32]
+    L.h2_autotune_tc.restype = ctypes.c_int
+    L.h2_autotune_tc.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int32]
+    L.h2_apply_tuning.restype = ctypes.c_int
+    L.h2_apply_tuning.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    L.h2_configure.restype = ctypes.c_int
+    L.h2_configure.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
     L.h2_device_status.restype = ctypes.c_int
     L.h2_device_status.argtypes = [ctypes.c_void_p]
     L.h2_status_string.restype = ctypes.c_char_p
@@ -144,6 +150,7 @@ def exported_symbols() -> list:
     """Names declared in include/h2.h (the C ABI)."""
     return ["h2_load", "h2_load_device", "h2_free", "h2_matvec", "h2_matvec_host", "h2_get_stats", "h2_sym_stats", "h2_sym_near", "h2_sym_near_stats",
             "h2_profile_matvec", "h2_gmres", "h2_gmres_batched", "h2_device_status", "h2_autotune",
+            "h2_autotune_tc", "h2_apply_tuning", "h2_configure",
             "h2_status_string", "h2_last_error"]
 
 
@@ -297,6 +304,7 @@ class H2Matrix:
         if wait_limit is not None:
             opts += f";wait_limit={int(wait_limit)}"
         torch.cuda.synchronize(device)
+        torch.cuda.empty_cache()   # the constructor's freed temporaries go back to the device
         h = ctypes.c_void_p()
         _check(lib().h2_load_device(ctypes.byref(tr), ctypes.byref(d), opts.encode(), ctypes.byref(h)),
                "h2_load_device")
@@ -434,12 +442,60 @@ class H2Matrix:
             _check(status, "h2_gmres_batched")
         return X, out
 
-    def autotune(self) -> dict:
-        """Pick the fastest CTA size of every product stage (returns the report)."""
+    def autotune(self, nrhs_tc: int | None = None, cache: str | None = None, fp32: bool = True) -> dict:
+        """Pick the fastest CTA size of every FP32 product stage and, with
+        nrhs_tc, the fastest pipeline depth of every tensor-core phase for that
+        many right-hand sides (returns the report). With `cache` (a JSON file),
+        a report stored for this GPU model and operator shape is applied
+        without timing anything, and a new report is stored there."""
         import json
-        buf = ctypes.create_string_buffer(1 << 16)
-        _check(lib().h2_autotune(self._h, buf, len(buf)), "h2_autotune")
-        return json.loads(buf.value.decode())
+        key = gpu = None
+        if cache:
+            import torch
+            gpu = torch.cuda.get_device_name(self.device)
+            st = self.stats()
+            key = (f"n={st['n']};clusters={st['n_clusters']};near={st['near_blocks']};adm={st['adm_blocks']};"
+                   f"max_rank={st['max_rank']};nrhs_tc={((nrhs_tc or 0) + 127) // 128 * 128}")
+            try:
+                with open(cache) as f:
+                    saved = json.load(f).get(gpu, {}).get(key)
+            except (OSError, ValueError):
+                saved = None
+            if saved:
+                _check(lib().h2_apply_tuning(self._h, json.dumps(saved).encode()), "h2_apply_tuning")
+                return dict(saved, cached=True)
+        buf = ctypes.create_string_buffer(1 << 18)
+        rep = {}
+        if fp32:
+            _check(lib().h2_autotune(self._h, buf, len(buf)), "h2_autotune")
+            rep = json.loads(buf.value.decode())
+        if nrhs_tc:
+            _check(lib().h2_autotune_tc(self._h, int(nrhs_tc), buf, len(buf)), "h2_autotune_tc")
+            rep.update(json.loads(buf.value.decode()))
+        if cache:
+            try:
+                with open(cache) as f:
+                    allc = json.load(f)
+            except (OSError, ValueError):
+                allc = {}
+            allc.setdefault(gpu, {})[key] = rep
+            d = os.path.dirname(os.path.abspath(cache))
+            os.makedirs(d, exist_ok=True)
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(allc, f)
+            os.replace(tmp, cache)
+        return rep
+
+    def configure(self, graphs: bool | None = None, tc_pipeline: bool | None = None):
+        """Change the graph and tensor-core pipeline options of the loaded handle."""
+        opts = []
+        if graphs is not None:
+            opts.append(f"graphs={int(bool(graphs))}")
+        if tc_pipeline is not None:
+            opts.append(f"tc_pipeline={int(bool(tc_pipeline))}")
+        if opts:
+            _check(lib().h2_configure(self._h, ";".join(opts).encode()), "h2_configure")
 
     def device_status(self) -> int:
         """Synchronise and return H2_OK or H2_ERR_TIMEOUT (a bounded wait ran out)."""

@@ -1,5 +1,6 @@
 """Full-size checks on the 32^3-voxel cube (N = 98,304, leaf 96, eps 1e-4):
-the H^2 data of the host constructor, the launch configuration bench.py times.
+the H^2 data of the GPU constructor loaded through h2_load_device, the launch
+configuration bench.py times.
 
 - FP32 product vs the oracle's FP64 H^2 product on the same data: 1e-5;
 - sampled rows against the oracle's dense VIE rows, evaluated one by one:
@@ -28,12 +29,14 @@ torch = pytest.importorskip("torch")
 
 @pytest.fixture(scope="module")
 def full():
-    from paper_1703_01175_gb300 import build, construct, h2
+    from paper_1703_01175_gb300 import build, construct_gpu, h2
     build.build_all()
     w = synth.workload("cube32")
     v = w.voxels
-    arrs, perm = construct.build_vie_h2_cached(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
-    A = h2.H2Matrix(arrs)
+    dh = construct_gpu.build_vie_h2_gpu(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
+    arrs, perm = dh.to_host(), dh.perm
+    A = h2.H2Matrix.from_device(dh)
+    dh.free()
     hZ = h2io.from_flat(arrs, perm)
     yield w, arrs, perm, A, hZ
     A.close()

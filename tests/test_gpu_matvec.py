@@ -173,6 +173,48 @@ def test_graph_replay_and_autotune(loaded):
         B.close()
 
 
+def test_split_graph_replay_and_tc_autotune(loaded, tmp_path):
+    """Split-bf16 product captured into a CUDA graph on first use and replayed
+    afterwards: bitwise equal to the directly launched product. Pipeline depths
+    chosen by h2_autotune_tc change no arithmetic order (bitwise equal product,
+    still within eps of the oracle), and a report cached for this GPU and
+    operator shape is applied to another handle without timing."""
+    from oracle import h2mv
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube12")
+    A = _mat(loaded, "cube12")
+    X = _colmajor(synth.random_complex(c.n, 14, cols=130))
+    Y1, Y2, Y3 = torch.empty_like(X), torch.empty_like(X), torch.empty_like(X)
+    A.configure(graphs=True)
+    try:
+        A.matvec(X, Y1, prec="splitbf16")      # captured
+        A.matvec(X, Y2, prec="splitbf16")      # another output: another graph
+        Y1.zero_()
+        A.matvec(X, Y1, prec="splitbf16")      # replayed
+        A.configure(graphs=False)
+        A.matvec(X, Y3, prec="splitbf16")      # direct launches
+        assert torch.equal(Y1, Y2) and torch.equal(Y1, Y3)
+        cache = str(tmp_path / "tune.json")
+        rep = A.autotune(nrhs_tc=130, cache=cache)
+        tc = {k: v for k, v in rep.items() if k.startswith("tc_")}
+        assert tc and all(2 <= v["ns"] <= 6 for v in tc.values())
+        Y4 = torch.empty_like(X)
+        A.matvec(X, Y4, prec="splitbf16")
+        assert torch.equal(Y4, Y3)
+        Y_or = h2mv.h2_dense(c.hZ) @ X.cpu().numpy().astype(np.complex128)
+        assert _rel(Y4.cpu().numpy(), Y_or) <= 1e-4
+        B = h2.H2Matrix(c.arrays())
+        try:
+            rb = B.autotune(nrhs_tc=130, cache=cache)
+            assert rb.get("cached") is True
+            assert {k: v["ns"] for k, v in rb.items() if k.startswith("tc_")} == {k: v["ns"] for k, v in tc.items()}
+            assert torch.equal(B.matvec(X, prec="splitbf16"), Y3)
+        finally:
+            B.close()
+    finally:
+        A.configure(graphs=True)
+
+
 def test_tensor_core_timeout_is_reported_and_context_survives(loaded):
     """Injected timeout: with a wait limit of 0 polls every first wait of the
     tensor-core kernels runs out; the kernels drain their copies, skip their

@@ -593,6 +593,16 @@ def run_ours(args, rank, world, local_rank):
                                   "sample": "one full FP64 H^2 product of the workload, BLAS on one thread"}
 
     A.close()
+    torch.cuda.empty_cache()
+    geos = None
+    if args.geometries:
+        geos = {}
+        for gname in ("slab256", "cube64v", "array4096"):
+            try:
+                geos[gname] = geometry_leg(gname, 5, 3, local_rank)
+            except Exception as e:  # a failed leg is reported, the headline stands
+                geos[gname] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
     if rank != 0:
         return
     launches = st["kernels_per_matvec"]
@@ -617,6 +627,7 @@ def run_ours(args, rank, world, local_rank):
                       "peak": hbm, "unit": "GB/s", "frac": near_gbs / hbm, "traffic": traffic,
                       "algorithmic_bytes_per_launch": near_bytes, "peak_source": peak_kind}),
         "symmetric_couplings": sym,
+        "geometries": geos,
         "stage_roofline": {"near": {"gbs": near_gbs, "frac": near_gbs / hbm, "bytes": near_bytes},
                            "couple": {"gbs": couple_gbs, "frac": couple_gbs / hbm, "bytes": couple_bytes}},
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
@@ -628,6 +639,14 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_geometry(args, local_rank):
+    line = geometry_leg(args.geometry, args.steps, args.warmup, local_rank)
+    print(json.dumps(line), flush=True)
+
+
+GEOMETRY_NRHS = {"slab256": 128, "cube64v": 256, "array4096": 256, "cube48": 32}
+
+
+def geometry_leg(geometry, steps, warmup, local_rank):
     """One of the paper's scaling geometries at full size (BASELINE configs 3
     and 5): H^2 data built on the GPU (construct_gpu, timed separately), loaded
     through h2_load_device; the FP32 single-RHS product and the split-bf16
@@ -640,7 +659,7 @@ def run_geometry(args, local_rank):
     build.build_all()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.workload(args.geometry)
+    w = synth.workload(geometry)
     v = w.voxels
     t0 = time.time()
     dh = construct_gpu.build_vie_h2_gpu(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps,
@@ -672,47 +691,51 @@ def run_geometry(args, local_rank):
     x = torch.from_numpy(synth.random_complex(n, 1).astype(np.complex64)).to(dev)
     y = torch.empty_like(x)
     A.autotune()
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         A.matvec(x, y)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local_rank) as clk:
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             A.matvec(x, y)
         e1.record()
         torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     bytes_fp32 = 8.0 * entries + 16.0 * n
-    R = w.nrhs
+    R = GEOMETRY_NRHS[geometry]
     Xm = torch.from_numpy(np.asfortranarray(synth.random_complex(n, 31, cols=R).astype(np.complex64)))
     Xm = Xm.to(dev).t().contiguous().t()
     Ym = torch.empty_like(Xm)
+    tc = A.autotune(nrhs_tc=R, fp32=False)
     for _ in range(3):
         A.matvec(Xm, Ym, prec="splitbf16")
     torch.cuda.synchronize(dev)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         A.matvec(Xm, Ym, prec="splitbf16")
     e1.record()
     torch.cuda.synchronize(dev)
-    ms_split = e0.elapsed_time(e1) / args.steps
+    ms_split = e0.elapsed_time(e1) / steps
     status = A.device_status()
     A.close()
+    del Xm, Ym, x, y
+    torch.cuda.empty_cache()
     bytes_split = 8.0 * entries + 2 * 8.0 * R * n   # hi and lo bf16 of Re and Im per stored entry; X read, Y written
     tensor_tflops = 24.0 * R * entries / (ms_split * 1e-3) / 1e12   # executed: 3 split products x 4 real MACs x 2
-    line = {"geometry": args.geometry, "n": n, "nrhs": R, "h2_build_s": round(t_build, 1),
+    line = {"geometry": geometry, "n": n, "nrhs": R, "h2_build_s": round(t_build, 1),
             "h2_build_stages_s": {k: round(v, 2) for k, v in build_info["seconds"].items()},
             "load_s": round(t_load, 2),
             "fp32": {"ms": ms, "gbs": bytes_fp32 / (ms * 1e-3) / 1e9, "frac_hbm": bytes_fp32 / (ms * 1e-3) / 1e9 / hbm,
                      "bytes": bytes_fp32},
             "splitbf16": {"ms": ms_split, "us_per_rhs": 1e3 * ms_split / R, "gbs": bytes_split / (ms_split * 1e-3) / 1e9,
                           "frac_hbm": bytes_split / (ms_split * 1e-3) / 1e9 / hbm, "tensor_tflops_executed": tensor_tflops,
-                          "tensor_frac_of_bf16_peak": tensor_tflops * 1e3 / _peaks_bf16(), "status": status},
+                          "tensor_frac_of_bf16_peak": tensor_tflops * 1e3 / _peaks_bf16(), "status": status,
+                          "pipeline_depths": {k: v["ns"] for k, v in tc.items()}},
             "bytes_per_unknown": bytes_fp32 / n, "stored_entries": entries, "max_rank": st["max_rank"],
             "near_blocks": st["near_blocks"], "adm_blocks": st["adm_blocks"], "levels": levels,
             "peak_gbs": hbm, "peak_source": peak_kind, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def fp_rates():
@@ -769,6 +792,8 @@ def main():
                     help="Arnoldi arithmetic of the --only-gmres cycle")
     ap.add_argument("--geometry", default=None, choices=["slab256", "cube64v", "array4096", "cube48"],
                     help="time one full-size scaling geometry built on the GPU and exit")
+    ap.add_argument("--no-geometries", dest="geometries", action="store_false",
+                    help="skip the full-size slab, 64^3 cube and cube-array legs (GPU construction, about 3 minutes)")
     ap.add_argument("--no-plain-batched", dest="plain_batched", action="store_false",
                     help="skip the batched plain GMRES arm (FP64 Arnoldi, about two minutes)")
     ap.add_argument("--only-matvec", action="store_true",

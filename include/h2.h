@@ -344,8 +344,10 @@ typedef struct {
                           summed with compensation, FP64 reductions, norms and
                           least squares; the stored vectors carry FP32
                           rounding, so tolerances well above 1e-7 only.
-                          1 and 2 are not available with precond = 1; with
-                          refine, 1 and 2 use the DFACC residual, 0 FP64ACC. */
+                          With precond = 1 the preconditioned directions are
+                          kept as c128 in every arithmetic (n x m x 16 bytes
+                          per right-hand side); with refine, 1 and 2 use the
+                          DFACC residual, 0 FP64ACC. */
     double reorth_eta; /* selective reorthogonalisation threshold eta in [0, 1]:
                           a second Gram-Schmidt projection when the first
                           leaves |w'| < eta |w| (Daniel, Gragg, Kaufman &
@@ -397,7 +399,11 @@ h2_status h2_gmres(h2_handle *h, const void *b, void *x, int32_t nrhs, int64_t l
  * whose residual estimate drops below tol / 2 stops contributing at the end
  * of the cycle. Restart residuals: accumulated products when opts->refine
  * (one per right-hand side; FP64ACC for arnoldi 0, DFACC for 1 and 2), else
- * one batched product with `prec`. opts->precond must be 0.
+ * one batched product with `prec`. opts->precond = 1: flexible GMRES with the
+ * handle's learned preconditioner (H2_ERR_STATE if none is loaded), applied
+ * to the basis vectors of all right-hand sides in one batched pass of the
+ * network; a right-hand side whose preconditioned cycle reduces its true
+ * residual by less than 5 % continues with plain GMRES.
  * b, x: device c128, nrhs columns with leading dimension ld >= N.
  * Workspace: an N x (m+1) x nrhs basis (16 bytes per entry for arnoldi 0
  * and 1, 8 for arnoldi 2) plus O(N nrhs) vectors, allocated on first use and

@@ -266,6 +266,27 @@ __global__ void arn_xupdate(ArnDev K, const double2 *__restrict__ basis, double2
     }
 }
 
+// basis column j of every right-hand side as c128 ([R][n]), whatever the
+// basis arithmetic: FP64 copy, c64 widened, double-float hi + lo
+__global__ void arn_basis_c128_kernel(ArnDev K, int mode, int j, double2 *__restrict__ out)
+{
+    const int r = blockIdx.y;
+    const size_t col = ((size_t)j * K.R + r) * K.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K.n; i += gridDim.x * blockDim.x) {
+        double2 v;
+        if (mode == ARN_F32) {
+            const float2 a = reinterpret_cast<const float2 *>(K.V)[col + i];
+            v = make_double2(a.x, a.y);
+        } else if (mode == ARN_DF) {
+            const float4 q = reinterpret_cast<const float4 *>(K.V)[col + i];
+            v = make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
+        } else {
+            v = K.V[col + i];
+        }
+        out[(size_t)r * K.n + i] = v;
+    }
+}
+
 __global__ void arn_to_c64(const double2 *__restrict__ a, int64_t lda, float2 *__restrict__ b, int n)
 {
     const int r = blockIdx.y;
@@ -793,8 +814,6 @@ h2_status arn_get(ArnWork **slot, int n, int m, int R, int extra_cols, int mode)
     arn_free(w);
     *slot = nullptr;
     if (mode != ARN_FP64 && mode != ARN_DF && mode != ARN_F32) return (set_error("GMRES: unknown Arnoldi arithmetic"), H2_ERR_ARG);
-    if (mode != ARN_FP64 && extra_cols)
-        return (set_error("GMRES: only the FP64 Arnoldi has a flexible variant"), H2_ERR_ARG);
     w = new ArnWork();
     w->n = n;
     w->m = m;
@@ -1037,12 +1056,21 @@ h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, 
     }
     ARNC(cudaMemcpyAsync(w->K.h1, w->h_hh, sizeof(double2) * w->R * (m + 2), cudaMemcpyHostToDevice, st));
     ARNC(cudaMemcpyAsync(w->K.kact, w->h_kact, sizeof(int) * w->R, cudaMemcpyHostToDevice, st));
-    if (w->mode == ARN_DF)
+    if (basis != w->K.V)   // flexible variant: the c128 preconditioned directions, every arithmetic
+        arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
+    else if (w->mode == ARN_DF)
         arn_xupdate_df<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, x, ldx);
     else if (w->mode == ARN_F32)
         arn_xupdate_f32<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, x, ldx);
     else
         arn_xupdate<<<vec_grid(w), 256, sizeof(double2) * (m + 2), st>>>(w->K, basis, x, ldx);
+    ARNC(cudaGetLastError());
+    return H2_OK;
+}
+
+h2_status arn_basis_c128(ArnWork *w, int j, double2 *out, cudaStream_t st)
+{
+    arn_basis_c128_kernel<<<vec_grid(w), 256, 0, st>>>(w->K, w->mode, j, out);
     ARNC(cudaGetLastError());
     return H2_OK;
 }

@@ -5,6 +5,10 @@
 // FP64 Arnoldi kernels of h2_arnoldi.cu are batched over the right-hand sides.
 // Restart residuals are recomputed with the FP64-accumulated product when
 // `refine` (iterative refinement), else with the batched FP32 product.
+// With the learned preconditioner (flexible GMRES, Saad 1993) the network is
+// applied to the basis vectors of all right-hand sides in one batched pass;
+// a right-hand side whose preconditioned cycle reduces its true residual by
+// less than 5 % continues with plain GMRES.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,12 +54,14 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
         return (set_error("h2_gmres_batched: need 1 <= restart <= 1024, maxit >= 1, tol > 0"), H2_ERR_ARG);
     if (prec != H2_PREC_FP32 && prec != H2_PREC_SPLITBF16)
         return (set_error("h2_gmres_batched: products must be H2_PREC_FP32 or H2_PREC_SPLITBF16"), H2_ERR_ARG);
-    if (opts->precond) return (set_error("h2_gmres_batched: no preconditioner in the batched solver"), H2_ERR_ARG);
+    const bool flexible = opts->precond != 0;
+    if (flexible && !h->precond)
+        return (set_error("h2_gmres_batched: no preconditioner loaded (h2_set_preconditioner)"), H2_ERR_STATE);
     h2::DeviceGuard dev_guard(h->device);
     if (dev_guard.err != cudaSuccess) return (set_error("h2_gmres_batched: cudaSetDevice failed"), H2_ERR_CUDA);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ArnWork *w = reinterpret_cast<ArnWork *>(h->bkrylov);
-    h2_status s = arn_get(&w, h->n, m, nrhs, 0, opts->arnoldi);
+    h2_status s = arn_get(&w, h->n, m, nrhs, flexible ? m : 0, opts->arnoldi);
     h->bkrylov = w;
     if (s != H2_OK) return s;
     if ((s = arn_set_eta(w, opts->reorth_eta)) != H2_OK) return s;
@@ -94,12 +100,34 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
     };
     int it = 0;
     std::vector<int> conv(R);
+    std::vector<char> pc(R, flexible ? 1 : 0);   // right-hand sides still preconditioned
+    // z_j = M(v_j) for every right-hand side in one pass of the network (the
+    // identity for those that fell back to plain GMRES); x32 = c64(z_j) is the
+    // product's input
+    auto precond_col = [&](int j) -> h2_status {
+        h2_status ps;
+        if ((ps = arn_basis_c128(w, j, w->tmp, st)) != H2_OK) return ps;
+        double2 *zc = w->Z + (size_t)j * R * n;
+        if ((ps = h2_apply_precond_batched(h, w->tmp, n, R, zc, n, w->x32, st)) != H2_OK) return ps;
+        bool any_off = false;
+        for (int r = 0; r < R; ++r)
+            if (!pc[r]) {
+                any_off = true;
+                if (cudaMemcpyAsync(zc + (size_t)r * n, w->tmp + (size_t)r * n, sizeof(double2) * n,
+                                    cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return (set_error("h2_gmres_batched: cudaMemcpyAsync failed"), H2_ERR_CUDA);
+            }
+        return any_off ? arn_c128_to_c64(w, zc, n, w->x32, st) : H2_OK;
+    };
+    std::vector<double> beta_start(R);
     while (update_active() > 0 && it < opts->maxit) {
         if ((s = arn_start(w, st)) != H2_OK) return s;
+        for (int r = 0; r < R; ++r) beta_start[r] = beta[r];
+        if (flexible && (s = precond_col(0)) != H2_OK) return s;
         std::fill(conv.begin(), conv.end(), -1);
         int k = 0;
         for (int j = 0; j < m && it < opts->maxit; ++j) {
-            if ((s = h2_matvec(h, arn_input(w, j), w->y32, R, n, prec, st)) != H2_OK) return s;
+            if ((s = h2_matvec(h, flexible ? w->x32 : arn_input(w, j), w->y32, R, n, prec, st)) != H2_OK) return s;
             if ((s = arn_step(w, j, st)) != H2_OK) return s;
             ++it;
             k = j + 1;
@@ -112,17 +140,21 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
                 else all = false;
             }
             if (all) break;
+            if (flexible && j + 1 < m && (s = precond_col(j + 1)) != H2_OK) return s;
         }
         for (int r = 0; r < R; ++r) {
             w->h_kact[r] = active[r] ? (conv[r] >= 0 ? conv[r] : k) : 0;
             if (active[r]) {
                 inf[r].iterations += w->h_kact[r];
                 ++inf[r].restarts;
+                if (pc[r]) ++inf[r].precond_cycles;
             }
         }
-        if ((s = arn_finish(w, w->K.V, x, ld, st)) != H2_OK) return s;
+        if ((s = arn_finish(w, flexible ? w->Z : w->K.V, x, ld, st)) != H2_OK) return s;
         if ((s = bk_true_residual(h, w, b, ld, x, ld, opts->refine != 0, prec, st)) != H2_OK) return s;
         if ((s = arn_read(w, st)) != H2_OK) return s;
+        for (int r = 0; r < R; ++r)   // a stagnating preconditioned cycle: plain GMRES for this right-hand side
+            if (pc[r] && active[r] && w->h_scal[8 * r] > 0.95 * beta_start[r]) pc[r] = 0;
     }
     update_active();
     h2_status worst = H2_OK;

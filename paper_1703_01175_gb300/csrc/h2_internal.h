@@ -165,7 +165,7 @@ struct ArnWork {
     ArnDev K{};
     int n = 0, m = 0, R = 0, extra_cols = 0, mode = ARN_FP64;
     int rows = 0, nbu = 0;          // row blocks of the update and residual passes
-    double2 *Z = nullptr;           // [extra_cols][R][n] preconditioned directions (flexible GMRES)
+    double2 *Z = nullptr;           // [extra_cols][R][n] preconditioned directions, c128 in every arithmetic (flexible GMRES)
     double2 *rr = nullptr, *tmp = nullptr;  // [R][n]
     float2 *x32 = nullptr, *y32 = nullptr;  // [R][n] product input / output
     double *h_scal = nullptr;       // pinned copy of scal
@@ -197,6 +197,8 @@ h2_status arn_read(ArnWork *w, cudaStream_t st);
 // least-squares solve (host) with h_kact columns, x_r += basis_r y_r
 h2_status arn_finish(ArnWork *w, const double2 *basis, double2 *x, int64_t ldx, cudaStream_t st);
 h2_status arn_c128_to_c64(ArnWork *w, const double2 *a, int64_t lda, float2 *b, cudaStream_t st);
+// basis column j of every right-hand side widened to c128, out [R][n]
+h2_status arn_basis_c128(ArnWork *w, int j, double2 *out, cudaStream_t st);
 h2_status arn_c64_to_c128(ArnWork *w, const float2 *a, double2 *b, cudaStream_t st);
 
 }  // namespace h2
@@ -298,6 +300,10 @@ void h2_free_bkrylov(h2_handle *h);
 void h2_free_bicgstab(h2_handle *h);
 // z = M(v) for one c128 vector (v of unit norm or any norm); also writes c64 z32 when not NULL
 h2_status h2_apply_precond(h2_handle *h, const double2 *v, double2 *z, float2 *z32, cudaStream_t st);
+// z_r = M(v_r) for R c128 vectors (v, z: [R][n] with strides ldv, ldz; z32: [R][n] c64 or NULL): one
+// pass of the network over a batch of R grids
+h2_status h2_apply_precond_batched(h2_handle *h, const double2 *v, int64_t ldv, int R, double2 *z, int64_t ldz,
+                                   float2 *z32, cudaStream_t st);
 h2_status h2_run_multi_f32(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                            cudaStream_t st);
 

@@ -92,7 +92,9 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
         while (beta / bnorm > opts->tol && it < opts->maxit) {
             const double beta_start = beta;
             if ((s = arn_start(w, st)) != H2_OK) return s;
-            if (pc && (s = h2_apply_precond(h, w->K.V, w->Z, w->x32, st)) != H2_OK) return s;
+            if (pc && ((s = arn_basis_c128(w, 0, w->tmp, st)) != H2_OK ||
+                       (s = h2_apply_precond(h, w->tmp, w->Z, w->x32, st)) != H2_OK))
+                return s;
             int k = 0;
             for (int j = 0; j < m && it < opts->maxit; ++j) {
                 if ((s = h2_matvec(h, pc ? w->x32 : arn_input(w, j), w->y32, 1, n, H2_PREC_FP32, st)) != H2_OK) return s;
@@ -108,8 +110,8 @@ h2_status h2_gmres(h2_handle *h, const void *b_, void *x_, int32_t nrhs, int64_t
                 const bool lucky = w->beta[0] <= 1e-14 * bnorm;
                 if (est <= 0.5 * opts->tol * bnorm || lucky) break;
                 if (pc && j + 1 < m &&
-                    (s = h2_apply_precond(h, w->K.V + (size_t)(j + 1) * n, w->Z + (size_t)(j + 1) * n, w->x32, st)) !=
-                        H2_OK)
+                    ((s = arn_basis_c128(w, j + 1, w->tmp, st)) != H2_OK ||
+                     (s = h2_apply_precond(h, w->tmp, w->Z + (size_t)(j + 1) * n, w->x32, st)) != H2_OK))
                     return s;
             }
             if (rs != H2_OK) break;

@@ -1,9 +1,11 @@
 // The learned preconditioner held by a handle: a 3-D convolutional network
 // on the voxel grid (weights and grid map copied from the caller), applied
-// to one vector at a time inside flexible GMRES (h2_krylov.cu).
+// to one vector inside flexible GMRES (h2_krylov.cu), or to the R vectors of
+// a batched solve in one pass of the network over R grids (h2_bkrylov.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -29,7 +31,49 @@ struct PrecondState {
     __nv_bfloat16 *act[2] = {nullptr, nullptr};
     float *out = nullptr;
     double *scale = nullptr;  // [0] = sqrt(3 nv) / |v|, [1] = its inverse (set per application)
+    int cmax = 8;
+    // batched application: activations and outputs of bcap grids, scales [2][bcap]
+    int bcap = 0;
+    __nv_bfloat16 *bact[2] = {nullptr, nullptr};
+    float *bout = nullptr;
+    double *bscale = nullptr;
 };
+
+// scale[r] = sqrt(n) / |v_r|, scale[R + r] = its inverse: one block per vector
+__global__ void set_scale_batched_kernel(const double2 *__restrict__ v, int64_t ldv, int n, int R, double *scale)
+{
+    const int r = blockIdx.x;
+    const double2 *x = v + (size_t)r * ldv;
+    double s = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[i].x * x[i].x + x[i].y * x[i].y;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        const double nrm = sqrt(t);
+        const double sc = nrm > 0 ? sqrt((double)n) / nrm : 1.0;
+        scale[r] = sc;
+        scale[R + r] = 1.0 / sc;
+    }
+}
+
+// z_r += v_r, and z32_r = c64(z_r) when z32 is not NULL
+__global__ void add_batched_kernel(double2 *__restrict__ z, int64_t ldz, const double2 *__restrict__ v, int64_t ldv,
+                                   float2 *__restrict__ z32, int n)
+{
+    const int r = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double2 a = z[(size_t)r * ldz + i];
+        const double2 b = v[(size_t)r * ldv + i];
+        a.x += b.x;
+        a.y += b.y;
+        z[(size_t)r * ldz + i] = a;
+        if (z32) z32[(size_t)r * n + i] = make_float2((float)a.x, (float)a.y);
+    }
+}
 
 __global__ void set_scale_kernel(const double2 *__restrict__ v, int n, double *scale)
 {
@@ -78,6 +122,10 @@ void free_state(PrecondState *P)
     cudaFree(P->act[1]);
     cudaFree(P->out);
     cudaFree(P->scale);
+    cudaFree(P->bact[0]);
+    cudaFree(P->bact[1]);
+    cudaFree(P->bout);
+    cudaFree(P->bscale);
     delete P;
 }
 
@@ -117,6 +165,56 @@ h2_status h2_apply_precond(h2_handle *h, const double2 *v, double2 *z, float2 *z
         if (cudaGetLastError() != cudaSuccess) return H2_ERR_CUDA;
     }
     return H2_OK;
+}
+
+h2_status h2_apply_precond_batched(h2_handle *h, const double2 *v, int64_t ldv, int R, double2 *z, int64_t ldz,
+                                   float2 *z32, cudaStream_t st)
+{
+    PrecondState *P = reinterpret_cast<PrecondState *>(h->precond);
+    if (!P) return H2_ERR_STATE;
+    if (R < 1) return H2_ERR_ARG;
+    if (R > P->bcap) {
+        cudaFree(P->bact[0]);
+        cudaFree(P->bact[1]);
+        cudaFree(P->bout);
+        cudaFree(P->bscale);
+        P->bact[0] = P->bact[1] = nullptr;
+        P->bout = nullptr;
+        P->bscale = nullptr;
+        P->bcap = 0;
+        const size_t act = (size_t)R * P->V * P->cmax * 2;
+        if (cudaMalloc(&P->bact[0], act) != cudaSuccess || cudaMalloc(&P->bact[1], act) != cudaSuccess ||
+            cudaMalloc(&P->bout, (size_t)R * P->V * 8 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&P->bscale, 2 * (size_t)R * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            h2::set_error("learned preconditioner: allocation of the batched activations failed");
+            return H2_ERR_ALLOC;
+        }
+        // grid voxels that are not unknowns read as zero input
+        if (cudaMemset(P->bact[0], 0, act) != cudaSuccess) return H2_ERR_CUDA;
+        P->bcap = R;
+    }
+    const int n = 3 * P->nv;
+    set_scale_batched_kernel<<<R, 1024, 0, st>>>(v, ldv, n, R, P->bscale);
+    if (P->nv < P->V) {  // grid voxels that are not unknowns read as zero (the layers reuse the buffer)
+        if (cudaMemsetAsync(P->bact[0], 0, (size_t)R * P->V * 8 * 2, st) != cudaSuccess) return H2_ERR_CUDA;
+    }
+    h2_status s = h2nn_pack(v, ldv, P->grid_of, P->aux, P->bscale, P->bact[0], R, P->nv, P->V, st);
+    if (s != H2_OK) return s;
+    int cur = 0;
+    for (size_t li = 0; li < P->layers.size(); ++li) {
+        const Layer &L = P->layers[li];
+        const bool last = li + 1 == P->layers.size();
+        s = h2nn_conv3d_fwd(P->bact[cur], L.w, L.b, last ? nullptr : P->bact[1 - cur], last ? P->bout : nullptr, R,
+                            P->Dx, P->Dy, P->Dz, L.ci, L.co, L.relu, st);
+        if (s != H2_OK) return s;
+        cur = 1 - cur;
+    }
+    s = h2nn_unpack(P->bout, P->layers.back().co, P->grid_of, P->bscale + R, z, ldz, R, P->nv, P->V, st);
+    if (s != H2_OK) return s;
+    dim3 g(std::min(1024, (n + 255) / 256), R);
+    add_batched_kernel<<<g, 256, 0, st>>>(z, ldz, v, ldv, z32, n);
+    return cudaGetLastError() == cudaSuccess ? H2_OK : H2_ERR_CUDA;
 }
 
 extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy, int32_t Dz,
@@ -166,6 +264,7 @@ extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy,
     P->Dz = Dz;
     P->V = V;
     P->nv = nv;
+    P->bcap = 0;
     auto fail = [&](const char *what) {
         cudaGetLastError();  // clear an out-of-memory result
         h2::set_error(std::string("h2_set_preconditioner: ") + what);
@@ -181,6 +280,7 @@ extern "C" h2_status h2_set_preconditioner(h2_handle *h, int32_t Dx, int32_t Dy,
         L.co = layer_spec[3 * l + 1];
         L.relu = layer_spec[3 * l + 2];
         cmax = std::max(cmax, std::max(L.ci, L.co));
+        P->cmax = cmax;
         const size_t nw = (size_t)L.co * 27 * L.ci;
         if (cudaMalloc(&L.w, nw * 2) != cudaSuccess || cudaMalloc(&L.b, L.co * sizeof(float)) != cudaSuccess) {
             P->layers.push_back(L);

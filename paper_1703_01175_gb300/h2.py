@@ -422,7 +422,7 @@ class H2Matrix:
         return y
 
     def gmres_batched(self, B, X=None, tol=1e-4, restart=50, maxit=1000, refine=False, x0_given=False,
-                      prec="splitbf16", arnoldi="fp64", reorth_eta=0.0, stream=None, check=True):
+                      prec="splitbf16", arnoldi="fp64", reorth_eta=0.0, stream=None, check=True, precond=False):
         """Batched GMRES for B (n, nrhs) column-major complex128 on the device."""
         import torch
         if B.dtype != torch.complex128 or not B.is_cuda:
@@ -430,14 +430,14 @@ class H2Matrix:
         nrhs, ld = self._shape(B)
         if X is None:
             X = torch.zeros_like(B)
-        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), 0,
+        opts = _SolveOpts(float(tol), int(restart), int(maxit), int(bool(refine)), int(bool(x0_given)), int(bool(precond)),
                           ARNOLDI[arnoldi], float(reorth_eta))
         infos = (_SolveInfo * nrhs)()
         st = torch.cuda.current_stream(B.device).cuda_stream if stream is None else stream
         status = lib().h2_gmres_batched(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()), nrhs,
                                         ld, ctypes.byref(opts), PREC[prec], infos, ctypes.c_void_p(st))
         out = [{"iterations": i.iterations, "restarts": i.restarts, "rel_res": i.rel_res, "status": i.status,
-                "reorth_steps": i.reorth_steps} for i in infos]
+                "reorth_steps": i.reorth_steps, "precond_cycles": i.precond_cycles} for i in infos]
         if check and status not in (H2_OK, H2_ERR_NOT_CONVERGED):
             _check(status, "h2_gmres_batched")
         return X, out

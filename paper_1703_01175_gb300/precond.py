@@ -227,6 +227,48 @@ def collect_pairs(A, gm: GridMap, rhs_list, restart=10, tol=1e-6, maxit=4000):
     return torch.stack(R), torch.stack(E)
 
 
+def collect_pairs_batched(A, B, restart=10, tol=1e-6, maxit=4000, pairs_per_rhs=50, prec="splitbf16",
+                          arnoldi="fp32", reorth_eta=0.1):
+    """Residual -> correction pairs from the method's own converged solves,
+    all right-hand sides in lockstep: batched GMRES(restart) from 0, one cycle
+    per call, keeping every restart iterate x_k of every right-hand side;
+    once b has converged to x*, up to `pairs_per_rhs` evenly spaced iterates
+    give the pairs (r_k, e_k) = (b - A x_k, x* - x_k), r_k from the
+    double-float-accumulated product. B: c128 (n, R) column-major on the
+    device. Returns c128 tensors R, E of shape [P, n] and the solve record."""
+    import torch
+    n, nr = B.shape
+    X = torch.zeros_like(B)
+    iters = [[] for _ in range(nr)]
+    done = [False] * nr
+    total = 0
+    while total < maxit and not all(done):
+        X, info = A.gmres_batched(B, X=X, tol=tol, restart=restart, maxit=restart, refine=True, x0_given=True,
+                                  prec=prec, arnoldi=arnoldi, reorth_eta=reorth_eta, check=False)
+        total += restart
+        for r in range(nr):
+            if done[r]:
+                continue
+            iters[r].append(X[:, r].clone())
+            if info[r]["status"] == 0:
+                done[r] = True
+    R, E = [], []
+    for r in range(nr):
+        if not done[r] or len(iters[r]) < 2:
+            continue
+        xs, cand = iters[r][-1], iters[r][:-1]
+        pick = np.unique(np.linspace(0, len(cand) - 1, min(pairs_per_rhs, len(cand))).round().astype(int))
+        bcol = B[:, r].contiguous()
+        for k in pick:
+            xk = cand[k]
+            R.append(bcol - A.matvec(xk.contiguous(), prec="dfacc"))
+            E.append(xs - xk)
+    record = {"rhs": nr, "converged": int(sum(done)), "steps": total, "restart": restart, "tol": tol}
+    if not R:
+        return None, None, record
+    return torch.stack(R), torch.stack(E), record
+
+
 def probe_pairs(A, count, seed=7, batch=32):
     """Probe pairs through the method's own product: e random (real and
     imaginary parts uniform in [-1, 1)), r = A e with the FP64-accumulated

@@ -189,3 +189,40 @@ def test_fgmres_identity_network_and_training():
         assert res2 <= 1e-6
     finally:
         A.close()
+
+
+@pytest.mark.parametrize("arnoldi", ["fp64", "df", "fp32"])
+def test_batched_fgmres_identity_network(arnoldi):
+    """Batched flexible GMRES with the learned-preconditioner machinery and the
+    identity network (M(v) = v): the preconditioned directions are the basis
+    vectors, so every right-hand side converges like plain batched GMRES (same
+    Arnoldi steps within 2) to the oracle's FP64 residual, in every Arnoldi
+    arithmetic, on the split-bf16 tensor-core products; and single-RHS FGMRES
+    runs in the same arithmetic."""
+    from paper_1703_01175_gb300 import h2 as h2py, precond as P
+    c = cases.get("cube12")
+    A = h2py.H2Matrix(c.arrays())
+    try:
+        gm = P.GridMap(c.v.shape, c.tree.perm, c.v.eps_r)
+        layers, W, Bs = P.identity_layers()
+        P.load_into(A, layers, W, Bs, gm)
+        R = 5
+        B = synth.random_plane_waves(c.v, R, seed=5)[c.tree.unknown_perm()]
+        Bt = torch.from_numpy(np.asfortranarray(B)).cuda().t().contiguous().t()
+        tol = 1e-5 if arnoldi == "fp32" else 1e-6
+        X0, i0 = A.gmres_batched(Bt, tol=tol, restart=25, maxit=600, refine=True, prec="splitbf16", arnoldi=arnoldi)
+        X1, i1 = A.gmres_batched(Bt, tol=tol, restart=25, maxit=600, refine=True, prec="splitbf16", arnoldi=arnoldi,
+                                 precond=True)
+        X1 = X1.cpu().numpy()
+        for j in range(R):
+            assert i1[j]["status"] == 0 and i1[j]["precond_cycles"] >= 1
+            assert abs(i1[j]["iterations"] - i0[j]["iterations"]) <= 2, (i0[j], i1[j])
+            res = np.linalg.norm(B[:, j] - c.oracle_matvec(X1[:, j])) / np.linalg.norm(B[:, j])
+            assert res <= 1.05 * tol
+        x2, i2 = A.gmres(torch.from_numpy(B[:, 0].copy()).cuda(), tol=tol, restart=25, maxit=600, refine=True,
+                         precond=1, arnoldi=arnoldi)
+        assert i2[0]["status"] == 0
+        res = np.linalg.norm(B[:, 0] - c.oracle_matvec(x2.cpu().numpy())) / np.linalg.norm(B[:, 0])
+        assert res <= 1.05 * tol
+    finally:
+        A.close()

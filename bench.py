@@ -102,12 +102,6 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def construct_cached(w):
-    from paper_1703_01175_gb300 import construct
-    v = w.voxels
-    return construct.build_vie_h2_cached(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps)
-
-
 # Selective reorthogonalisation threshold of the "new" solves: one projection
 # keeps w' orthogonal to the basis to about u / eta (Daniel et al. 1976), 10 u
 # here; the plain solve keeps the classical eta = 1/sqrt(2).
@@ -526,42 +520,12 @@ def run_ours(args, rank, world, local_rank):
         gm["new_vs_plain_per_rhs"] = gm["plain_m%d" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
         gm["new_vs_plain_df_per_rhs"] = gm["plain_m%d_df" % m_new]["ms"] / gm["new_batched"]["ms_per_rhs"]
 
-    # learned preconditioner (shipped weights, trained by train_precond on the 16^3 cube): flexible
-    # GMRES(50) with M(v) = v + N(v) against plain GMRES(50), on the bench cube and on the training cube
-    wpath = os.path.join(ROOT, "paper_1703_01175_gb300", "weights", "vie_u26.npz")
+    # learned preconditioner (config 4): the network trained by train_precond on pairs from the method's own
+    # solves of the 48^3 smooth-permittivity cube, as the right preconditioner of batched flexible GMRES(m)
+    # (split-bf16 products, c64-basis Arnoldi) against plain batched GMRES(m) on 32 held-out plane waves
+    wpath = os.path.join(ROOT, "paper_1703_01175_gb300", "weights", "vie_cube48.npz")
     if args.learned and os.path.exists(wpath):
-        from paper_1703_01175_gb300 import precond as P
-        z = np.load(wpath)
-        layers = [tuple(int(v) for v in x) for x in z["layers"]]
-        Wl = [z[f"W{i}"] for i in range(len(layers))]
-        Bl = [z[f"b{i}"] for i in range(len(layers))]
-        learned = {"weights": os.path.relpath(wpath, ROOT), "n_params": int(sum(x.size for x in Wl) + sum(x.size for x in Bl))}
-        for wname in ("cube16r", WORKLOAD):
-            if wname == WORKLOAD:
-                Aw, pw, ww = A, perm, w
-            else:
-                ww = synth.workload(wname)
-                aw, pw = construct_cached(ww)
-                Aw = h2py.H2Matrix(aw, device=local_rank)
-            gmw = P.GridMap(ww.voxels.shape, pw, ww.voxels.eps_r)
-            P.load_into(Aw, layers, Wl, Bl, gmw)
-            bw = torch.from_numpy(synth.default_rhs(ww)[(3 * pw[:, None] + np.arange(3)[None, :]).reshape(-1)]).to(dev)
-            row = {}
-            for label, pc in (("plain", 0), ("fgmres_learned", 1)):
-                torch.cuda.synchronize(dev)
-                g0 = torch.cuda.Event(enable_timing=True)
-                g1 = torch.cuda.Event(enable_timing=True)
-                g0.record(stream)
-                xs, info = Aw.gmres(bw, tol=ww.tol, restart=50, maxit=2000, refine=True, precond=pc)
-                g1.record(stream)
-                torch.cuda.synchronize(dev)
-                row[label] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
-                              "rel_res": info[0]["rel_res"], "status": info[0]["status"],
-                              "precond_cycles": info[0]["precond_cycles"]}
-            learned[wname] = row
-            if Aw is not A:
-                Aw.close()
-        gm["learned"] = learned
+        gm["learned"] = learned_leg(wpath, local_rank, dev, stream)
 
     # end to end through the host-pointer entry point
     for _ in range(2):
@@ -738,6 +702,114 @@ def geometry_leg(geometry, steps, warmup, local_rank):
     return line
 
 
+def learned_leg(wpath, local_rank, dev, stream, nrhs=32, restart=50, maxit=3000):
+    """Batched FGMRES with the trained network against plain batched GMRES on
+    held-out plane waves (seed 6) of the 48^3 smooth-permittivity cube; the
+    time ratio is quoted only when both arms converged on every right-hand
+    side."""
+    import torch
+    import synth
+    from paper_1703_01175_gb300 import precond as P, h2 as h2py
+    z = np.load(wpath)
+    rec = json.loads(str(z["record"])) if "record" in z.files else {}
+    layers = [tuple(int(v) for v in x) for x in z["layers"]]
+    Wl = [z[f"W{i}"] for i in range(len(layers))]
+    Bl = [z[f"b{i}"] for i in range(len(layers))]
+    wname = rec.get("train_workload", "cube48")
+    w, arrs, perm, t_build, dh = build_workload_gpu(wname, local_rank)
+    del arrs
+    Aw = h2py.H2Matrix.from_device(dh, device=local_rank)
+    dh.free()
+    del dh
+    out = {"weights": os.path.relpath(wpath, ROOT), "workload": wname, "n": Aw.n, "nrhs": nrhs, "restart": restart,
+           "n_params": int(sum(x.size for x in Wl) + sum(x.size for x in Bl)),
+           "training": {k: rec.get(k) for k in ("pairs", "solve_pairs", "probe_pairs", "loss", "epochs")}}
+    try:
+        gmw = P.GridMap(w.voxels.shape, perm, w.voxels.eps_r)
+        P.load_into(Aw, layers, Wl, Bl, gmw)
+        unk = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)
+        B = synth.random_plane_waves(w.voxels, nrhs, seed=6)[unk]
+        Bt = torch.from_numpy(np.asfortranarray(B)).to(dev).t().contiguous().t()
+        for label, pc in (("plain", False), ("fgmres_learned", True)):
+            Aw.gmres_batched(Bt, tol=1e-12, restart=4, maxit=4, refine=True, prec="splitbf16", arnoldi="fp32",
+                             reorth_eta=NEW_ETA, precond=pc, check=False)   # workspace, images
+            torch.cuda.synchronize(dev)
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            X, info = Aw.gmres_batched(Bt, tol=w.tol, restart=restart, maxit=maxit, refine=True, prec="splitbf16",
+                                       arnoldi="fp32", reorth_eta=NEW_ETA, precond=pc, check=False)
+            g1.record(stream)
+            torch.cuda.synchronize(dev)
+            out[label] = {"ms_total": g0.elapsed_time(g1), "ms_per_rhs": g0.elapsed_time(g1) / nrhs,
+                          "converged": sum(1 for i in info if i["status"] == 0),
+                          "mean_iterations": float(np.mean([i["iterations"] for i in info])),
+                          "max_rel_res": max(i["rel_res"] for i in info),
+                          "mean_precond_cycles": float(np.mean([i["precond_cycles"] for i in info]))}
+            del X
+        both = out["plain"]["converged"] == nrhs and out["fgmres_learned"]["converged"] == nrhs
+        out["both_converged"] = both
+        out["time_ratio_plain_over_learned"] = (out["plain"]["ms_total"] / out["fgmres_learned"]["ms_total"]
+                                                if both else None)
+    finally:
+        Aw.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def nn_timing(steps=20, dims=(48, 48, 48)):
+    """CUDA-event times of the learned preconditioner's tensor-core
+    convolutions on the 48^3 grid (32 -> 32 channels, the hidden layers of the
+    network): forward for batches of 1 and 32 grids, weight gradient for a
+    training batch of 8; with the executed tensor flops against the bf16
+    peak (the forward counts 2 x 27 x 32 x 32 flops per voxel, the weight
+    gradient the same twice for its hi and lo dz products)."""
+    import torch
+    from paper_1703_01175_gb300 import build, precond as P
+    build.build_all()
+    V = dims[0] * dims[1] * dims[2]
+    out = {"grid": list(dims), "cin": 32, "cout": 32}
+    g = torch.Generator(device="cuda").manual_seed(3)
+    w = (torch.randn(32 * 27 * 32, device="cuda", generator=g) * 0.05).to(torch.bfloat16)
+    bias = torch.zeros(32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for B in (1, 32):
+        x = torch.randn(B * V * 32, device="cuda", generator=g).to(torch.bfloat16)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            P._call("h2nn_conv3d_fwd", P._p(x), P._p(w), P._p(bias), P._p(y), None, B, *dims, 32, 32, 1, st)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            P._call("h2nn_conv3d_fwd", P._p(x), P._p(w), P._p(bias), P._p(y), None, B, *dims, 32, 32, 1, st)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        fl = 2.0 * 27 * 32 * 32 * V * B
+        out[f"fwd_B{B}"] = {"ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                            "frac_bf16_peak": fl / (ms * 1e-3) / 1e9 / _peaks_bf16()}
+        del x, y
+    B = 8
+    x = torch.randn(B * V * 32, device="cuda", generator=g).to(torch.bfloat16)
+    dz = torch.randn(B * V * 32, device="cuda", generator=g)
+    dw = torch.empty(32 * 27 * 32, device="cuda")
+    db = torch.empty(32, device="cuda")
+    for _ in range(3):
+        P._call("h2nn_conv3d_bwd_weight", P._p(dz), P._p(x), P._p(dw), P._p(db), B, *dims, 32, 32, 0, st)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        P._call("h2nn_conv3d_bwd_weight", P._p(dz), P._p(x), P._p(dw), P._p(db), B, *dims, 32, 32, 0, st)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    fl = 2.0 * 2.0 * 27 * 32 * 32 * V * B
+    out["bwd_weight_B8"] = {"ms": ms, "tflops": fl / (ms * 1e-3) / 1e12,
+                            "frac_bf16_peak": fl / (ms * 1e-3) / 1e9 / _peaks_bf16()}
+    out["status"] = P._nnlib().h2nn_device_status()
+    print(json.dumps({"nn_timing": out}), flush=True)
+
+
 def fp_rates():
     """FP64 and FP32 (tensor cores off) GEMM throughput of cuda:0 with cuBLAS:
     the ceilings of the FP64 Gram-Schmidt passes and of their double-float
@@ -778,6 +850,8 @@ def main():
     ap.add_argument("--mrhs", type=int, default=128, help="right-hand sides of the multi-RHS leg (0: skip)")
     ap.add_argument("--no-sym", dest="sym", action="store_false",
                     help="skip the product with couplings stored once per admissible pair")
+    ap.add_argument("--nn", action="store_true",
+                    help="time the learned preconditioner's convolutions on the 48^3 grid and exit")
     ap.add_argument("--fp-rates", action="store_true",
                     help="print the FP64 and FP32 (non-tensor) GEMM rates of the GPU and exit")
     ap.add_argument("--mrhs-prec", default="splitbf16", choices=["splitbf16", "fp32"],
@@ -801,6 +875,9 @@ def main():
     args = ap.parse_args()
     if args.fp_rates:
         fp_rates()
+        return
+    if args.nn:
+        nn_timing(args.steps)
         return
     if args.geometry:
         run_geometry(args, int(os.environ.get("LOCAL_RANK", "0")))

@@ -27,8 +27,9 @@ extern "C" {
 #endif
 
 /*
- * Forward convolution (implicit GEMM, M = voxels, N = Cout, K = 27 Cin, bf16
- * products on the tensor cores, FP32 accumulation):
+ * Forward convolution (implicit GEMM on the tcgen05 tensor cores: M = 128
+ * voxels per tile, N = Cout, K = 27 taps x Cin, bf16 products, FP32
+ * accumulation in tensor memory):
  *   z[b][v][co] = bias[co] + sum_{t,ci} w[co][t][ci] in[b][v + off(t)][ci]
  *   out = ReLU(z) when relu != 0, else z.
  * in, w: bf16; bias: f32 or NULL; out_bf16 (bf16) and/or out_f32 (f32) may
@@ -49,11 +50,18 @@ h2_status h2nn_flip_weights(const void *w, void *wt, int32_t Cin, int32_t Cout, 
  * Weight and bias gradients: dw[co][t][ci] (+)= sum_{b,v} dz[b][v][co] in[b][v + off(t)][ci],
  * db[co] (+)= sum_{b,v} dz[b][v][co]. dz: f32 [B][V][Cout]; in: bf16;
  * dw, db: f32 (db may be NULL). accumulate = 0 overwrites, 1 adds.
- * FP32 accumulation on CUDA cores.
+ * dw on the tcgen05 tensor cores: M = (tap, ci) pairs, N = Cout, K = voxels;
+ * in is bf16 (exact), dz is split into bf16 hi + lo and both products are
+ * accumulated in FP32 (about 16 significant bits per term); db on CUDA cores.
  */
 h2_status h2nn_conv3d_bwd_weight(const float *dz, const void *in, float *dw, float *db, int32_t B, int32_t Dx,
                                  int32_t Dy, int32_t Dz, int32_t Cin, int32_t Cout, int32_t accumulate,
                                  void *stream);
+
+/* H2_ERR_TIMEOUT if a bounded wait inside a tensor-core convolution ran out
+   since the last call (that launch skipped its output), else H2_OK;
+   synchronises the device and clears the flag. */
+h2_status h2nn_device_status(void);
 
 /* dz = dy * (y > 0) (ReLU backward from the layer's output y), count entries;
    dy f32, y bf16, dz f32 (dz may alias dy). */

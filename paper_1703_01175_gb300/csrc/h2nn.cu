@@ -1,5 +1,5 @@
-// Kernels of the learned preconditioner (include/h2nn.h): 3x3x3 convolutions
-// as implicit GEMMs on the tensor cores (bf16 in, FP32 accumulate), their
+// Kernels of the learned preconditioner (include/h2nn.h): the entry points of
+// the 3x3x3 convolutions (tcgen05 implicit GEMMs in h2nn_tc.cu), bias
 // gradients, ReLU backward, a relative mean-square loss, Adam, and the
 // mapping between tree-order residual vectors and channel-last voxel grids.
 #include <cuda_bf16.h>
@@ -12,101 +12,15 @@
 #include "h2nn.h"
 
 namespace h2 {
-namespace {
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ bool neighbour(int v, int tap, int Dx, int Dy, int Dz, int &nv)
-{
-    const int x = v % Dx, y = (v / Dx) % Dy, z = v / (Dx * Dy);
-    const int nx = x + tap % 3 - 1, ny = y + (tap / 3) % 3 - 1, nz = z + tap / 9 - 1;
-    if (nx < 0 || ny < 0 || nz < 0 || nx >= Dx || ny >= Dy || nz >= Dz) return false;
-    nv = nx + Dx * (ny + Dy * nz);
-    return true;
-}
-
-// Implicit-GEMM convolution: a CTA owns 64 voxels of one sample and all Cout
-// channels; each of its 4 warps computes a 16-voxel x Cout block with
-// m16n8k16 bf16 tensor-core MMAs over K = 27 Cin in steps of 16.
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128)
-conv_fwd_kernel(const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
-                const float *__restrict__ bias, __nv_bfloat16 *__restrict__ out_bf, float *__restrict__ out_f,
-                int Dx, int Dy, int Dz, int relu)
-{
-    constexpr int K = 27 * CIN;
-    constexpr int KS = (K + 15) / 16;
-    constexpr int NT = COUT / 8;
-    __shared__ __align__(16) __nv_bfloat16 As[64][24];
-    __shared__ __align__(16) __nv_bfloat16 Bs[COUT][24];
-    const int V = Dx * Dy * Dz;
-    const int b = blockIdx.y;
-    const int v0 = blockIdx.x * 64;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, c = lane & 3;
-    const int arow = tid >> 1, achunk = tid & 1;
-    const int va = v0 + arow;
-    const __nv_bfloat16 *inb = in + (size_t)b * V * CIN;
-    float acc[NT][4];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
+cudaError_t launch_fwd_tc(const void *in, const void *w, const float *bias, void *out_bf16, float *out_f32, int B,
+                          int Dx, int Dy, int Dz, int relu, cudaStream_t st);
+template <int CIN, int COUT>
+cudaError_t launch_bwdw_tc(const float *dz, const void *in, float *dw, int B, int Dx, int Dy, int Dz, cudaStream_t st);
+int nn_tc_take_error();
 
-    for (int ks = 0; ks < KS; ++ks) {
-        {
-            const int k = ks * 16 + achunk * 8;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            int nv;
-            if (va < V && k < K && neighbour(va, k / CIN, Dx, Dy, Dz, nv))
-                val = *reinterpret_cast<const uint4 *>(inb + (size_t)nv * CIN + (k % CIN));
-            *reinterpret_cast<uint4 *>(&As[arow][achunk * 8]) = val;
-        }
-        if (tid < COUT * 2) {
-            const int co = tid >> 1, ch = tid & 1;
-            const int kb = ks * 16 + ch * 8;
-            uint4 wv = make_uint4(0, 0, 0, 0);
-            if (kb < K) wv = *reinterpret_cast<const uint4 *>(w + (size_t)co * K + kb);
-            *reinterpret_cast<uint4 *>(&Bs[co][ch * 8]) = wv;
-        }
-        __syncthreads();
-        uint32_t a[4];
-        const int r = warp * 16 + g;
-        a[0] = *reinterpret_cast<const uint32_t *>(&As[r][2 * c]);
-        a[1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * c]);
-        a[2] = *reinterpret_cast<const uint32_t *>(&As[r][2 * c + 8]);
-        a[3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][2 * c + 8]);
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const uint32_t b0 = *reinterpret_cast<const uint32_t *>(&Bs[t * 8 + g][2 * c]);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t *>(&Bs[t * 8 + g][2 * c + 8]);
-            mma_bf16_16816(acc[t], a, b0, b1);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const int co = t * 8 + 2 * c;
-        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int v = v0 + warp * 16 + g + 8 * h;
-            if (v >= V) continue;
-            float x0 = acc[t][2 * h] + b0, x1 = acc[t][2 * h + 1] + b1;
-            if (relu) {
-                x0 = fmaxf(x0, 0.f);
-                x1 = fmaxf(x1, 0.f);
-            }
-            const size_t o = ((size_t)b * V + v) * COUT + co;
-            if (out_bf) *reinterpret_cast<__nv_bfloat162 *>(out_bf + o) = __floats2bfloat162_rn(x0, x1);
-            if (out_f) *reinterpret_cast<float2 *>(out_f + o) = make_float2(x0, x1);
-        }
-    }
-}
+namespace {
 
 __global__ void flip_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *__restrict__ wt, int Cin, int Cout)
 {
@@ -114,62 +28,6 @@ __global__ void flip_kernel(const __nv_bfloat16 *__restrict__ w, __nv_bfloat16 *
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int ci = i % Cin, t = (i / Cin) % 27, co = i / (27 * Cin);
         wt[((size_t)ci * 27 + (26 - t)) * Cout + co] = w[i];
-    }
-}
-
-// dw[co][t][ci] += sum dz[b][v][co] in[b][v + off(t)][ci]: one CTA per (tap,
-// voxel chunk); the CTA loops over samples and 64-voxel tiles.
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256)
-conv_bwdw_kernel(const float *__restrict__ dz, const __nv_bfloat16 *__restrict__ in, float *__restrict__ dw,
-                 int B, int Dx, int Dy, int Dz, int vchunk)
-{
-    constexpr int TV = 64;
-    constexpr int NP = (CIN * COUT + 255) / 256;
-    __shared__ float dzs[TV][COUT];
-    __shared__ float ins[TV][CIN + 1];
-    const int V = Dx * Dy * Dz;
-    const int tap = blockIdx.x;
-    const int vbeg = blockIdx.y * vchunk, vend = min(V, vbeg + vchunk);
-    float acc[NP];
-#pragma unroll
-    for (int q = 0; q < NP; ++q) acc[q] = 0.f;
-    for (int b = 0; b < B; ++b) {
-        for (int t0 = vbeg; t0 < vend; t0 += TV) {
-            for (int e = threadIdx.x; e < TV * COUT; e += 256) {
-                const int tv = e / COUT, co = e % COUT, v = t0 + tv;
-                dzs[tv][co] = v < vend ? dz[((size_t)b * V + v) * COUT + co] : 0.f;
-            }
-            for (int e = threadIdx.x; e < TV * CIN; e += 256) {
-                const int tv = e / CIN, ci = e % CIN, v = t0 + tv;
-                int nv;
-                float val = 0.f;
-                if (v < vend && neighbour(v, tap, Dx, Dy, Dz, nv))
-                    val = __bfloat162float(in[((size_t)b * V + nv) * CIN + ci]);
-                ins[tv][ci] = val;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                const int p = threadIdx.x + 256 * q;
-                if (p < CIN * COUT) {
-                    const int co = p / CIN, ci = p % CIN;
-                    float s = 0.f;
-#pragma unroll 8
-                    for (int tv = 0; tv < TV; ++tv) s += dzs[tv][co] * ins[tv][ci];
-                    acc[q] += s;
-                }
-            }
-            __syncthreads();
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        const int p = threadIdx.x + 256 * q;
-        if (p < CIN * COUT) {
-            const int co = p / CIN, ci = p % CIN;
-            atomicAdd(&dw[((size_t)co * 27 + tap) * CIN + ci], acc[q]);
-        }
     }
 }
 
@@ -301,29 +159,6 @@ inline int gridsz(int64_t n, int bs = 256) { return (int)std::min<int64_t>(4096,
 
 }  // namespace
 
-template <int CIN, int COUT>
-static cudaError_t launch_fwd(const void *in, const void *w, const float *bias, void *ob, float *of, int B, int Dx,
-                              int Dy, int Dz, int relu, cudaStream_t st)
-{
-    const int V = Dx * Dy * Dz;
-    dim3 grid((V + 63) / 64, B);
-    conv_fwd_kernel<CIN, COUT><<<grid, 128, 0, st>>>(
-        reinterpret_cast<const __nv_bfloat16 *>(in), reinterpret_cast<const __nv_bfloat16 *>(w), bias,
-        reinterpret_cast<__nv_bfloat16 *>(ob), of, Dx, Dy, Dz, relu);
-    return cudaGetLastError();
-}
-
-template <int CIN, int COUT>
-static cudaError_t launch_bwdw(const float *dz, const void *in, float *dw, int B, int Dx, int Dy, int Dz,
-                               cudaStream_t st)
-{
-    const int V = Dx * Dy * Dz;
-    const int vchunk = 2048;
-    dim3 grid(27, (V + vchunk - 1) / vchunk);
-    conv_bwdw_kernel<CIN, COUT><<<grid, 256, 0, st>>>(dz, reinterpret_cast<const __nv_bfloat16 *>(in), dw, B, Dx, Dy,
-                                                      Dz, vchunk);
-    return cudaGetLastError();
-}
 
 }  // namespace h2
 
@@ -352,7 +187,7 @@ h2_status h2nn_conv3d_fwd(const void *in, const void *w, const float *bias, void
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaErrorInvalidValue;
 #define H2NN_FWD(ci, co)                                                                          \
-    if (Cin == ci && Cout == co) e = launch_fwd<ci, co>(in, w, bias, out_bf16, out_f32, B, Dx, Dy, Dz, relu, st);
+    if (Cin == ci && Cout == co) e = launch_fwd_tc<ci, co>(in, w, bias, out_bf16, out_f32, B, Dx, Dy, Dz, relu, st);
     H2NN_FWD(8, 8) H2NN_FWD(8, 16) H2NN_FWD(8, 32) H2NN_FWD(16, 8) H2NN_FWD(16, 16) H2NN_FWD(16, 32)
     H2NN_FWD(32, 8) H2NN_FWD(32, 16) H2NN_FWD(32, 32)
 #undef H2NN_FWD
@@ -388,7 +223,7 @@ h2_status h2nn_conv3d_bwd_weight(const float *dz, const void *in, float *dw, flo
     }
     e = cudaErrorInvalidValue;
 #define H2NN_BW(ci, co) \
-    if (Cin == ci && Cout == co) e = launch_bwdw<ci, co>(dz, in, dw, B, Dx, Dy, Dz, st);
+    if (Cin == ci && Cout == co) e = launch_bwdw_tc<ci, co>(dz, in, dw, B, Dx, Dy, Dz, st);
     H2NN_BW(8, 8) H2NN_BW(8, 16) H2NN_BW(8, 32) H2NN_BW(16, 8) H2NN_BW(16, 16) H2NN_BW(16, 32)
     H2NN_BW(32, 8) H2NN_BW(32, 16) H2NN_BW(32, 32)
 #undef H2NN_BW
@@ -482,6 +317,21 @@ h2_status h2nn_unpack(const float *chan, int32_t C, const int32_t *grid_of, cons
     unpack_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
         chan, C, grid_of, scale, reinterpret_cast<double2 *>(vec), ldv, nv, V);
     return nn_err(cudaGetLastError(), "h2nn_unpack");
+}
+
+h2_status h2nn_device_status(void)
+{
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        set_error("h2nn_device_status: device synchronisation failed");
+        return H2_ERR_CUDA;
+    }
+    const int f = nn_tc_take_error();
+    if (f < 0) {
+        set_error("h2nn_device_status: reading the error flag failed");
+        return H2_ERR_CUDA;
+    }
+    return f ? H2_ERR_TIMEOUT : H2_OK;
 }
 
 }  // extern "C"

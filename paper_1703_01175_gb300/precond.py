@@ -41,6 +41,7 @@ def _nnlib():
         "h2nn_pack": [fp, i64, fp, fp, fp, fp, i32, i32, i64, fp],
         "h2nn_unpack": [fp, i32, fp, fp, fp, i64, i32, i32, i64, fp],
         "h2_set_preconditioner": [fp, i32, i32, i32, fp, fp, i32, fp, fp, fp],
+        "h2nn_device_status": [],
     }
     for name, args in sig.items():
         f = getattr(L, name)

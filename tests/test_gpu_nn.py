@@ -226,3 +226,10 @@ def test_batched_fgmres_identity_network(arnoldi):
         assert res <= 1.05 * tol
     finally:
         A.close()
+
+
+def test_tensor_core_convolutions_report_no_timeout():
+    """The tcgen05 convolutions' bounded waits did not run out in this
+    session's launches (h2nn_device_status)."""
+    from paper_1703_01175_gb300 import precond as P
+    assert P._nnlib().h2nn_device_status() == 0

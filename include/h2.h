@@ -117,9 +117,10 @@ typedef struct {
  * afterwards; at most 8 graphs of each kind are kept, least recently used
  * first out), "tc_pipeline=0|1" (default 1: the split-bf16 tensor-core kernel runs
  * the deepest pipeline that fits in shared memory, up to 6 stages; 0: two),
- * "wait_limit=N" (polls of every bounded wait inside the tensor-core kernels,
- * default 2^24; when one runs out the kernel waits for its copies and MMAs in
- * flight, skips its output, frees its tensor memory and flags the handle, so
+ * "wait_limit=N" (polls of every bounded wait inside the tensor-core kernels
+ * and the bulk-copy pipeline of the symmetric-storage kernel, default 2^24;
+ * when one runs out the kernel waits for its copies and MMAs in flight, skips
+ * its output, frees its tensor memory and flags the handle, so
  * that h2_device_status returns H2_ERR_TIMEOUT; 0 makes every first wait run
  * out, which tests that path), "sym_couple=0|1" (default 0; 1: the single-RHS
  * FP32 product keeps each coupling once per admissible pair, S^{t,s} with
@@ -191,16 +192,21 @@ h2_status h2_matvec_host(h2_handle *h, const void *x_host, void *y_host,
                          int32_t nrhs, int64_t ld, h2_prec prec);
 
 /* Synchronise the handle's device and report H2_ERR_TIMEOUT if a bounded wait
-   inside a tensor-core kernel ran out since the handle was loaded (the
-   kernel then skipped its output), else H2_OK. */
+   inside a tensor-core kernel or the symmetric-storage kernel ran out since
+   the handle was loaded (the kernel then skipped its output), else H2_OK. */
 h2_status h2_device_status(h2_handle *h);
 
 /*
  * Autotune the launch shape of every stage of the FP32 product: for each
  * block-row phase, time each admissible CTA size (128 ... 1024 threads) with
- * CUDA events and keep the fastest. Writes a JSON report (phase -> chosen
- * threads, time in microseconds, all candidates) into report[0..report_len)
- * when report is not NULL. Synchronous; drops cached graphs.
+ * CUDA events and keep the fastest. With symmetric storage (sym_couple=1, and
+ * the near field after h2_sym_near) it also times the two launch shapes of
+ * the dual kernel (160 threads: 4 consumer warps, three CTAs per SM; 288: 8
+ * consumer warps, two CTAs per SM), entries "sym_couple" and "sym_near";
+ * building the symmetric couplings first if needed. Writes a JSON report
+ * (phase -> chosen threads, time in microseconds, all candidates) into
+ * report[0..report_len) when report is not NULL. Synchronous; drops cached
+ * graphs.
  */
 h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len);
 
@@ -221,9 +227,10 @@ h2_status h2_autotune_tc(h2_handle *h, int32_t nrhs, char *report, int32_t repor
  * Apply a report of h2_autotune or h2_autotune_tc (for instance one cached
  * from an earlier run on the same GPU and operator shape) without timing
  * anything: "<phase>": {"threads": N} sets a CTA size (a multiple of 32 in
- * [rows / 2, 1024]), "<phase>": {"ns": N} a tensor-core pipeline depth
- * (0 ... 6; 0 = deepest that fits). H2_ERR_ARG for an unknown phase or a bad
- * value. Drops captured graphs.
+ * [rows / 2, 1024]; 160 or 288 for "sym_couple" and "sym_near"),
+ * "<phase>": {"ns": N} a tensor-core pipeline depth (0 ... 6; 0 = deepest
+ * that fits). H2_ERR_ARG for an unknown phase or a bad value. Drops captured
+ * graphs.
  */
 h2_status h2_apply_tuning(h2_handle *h, const char *report);
 

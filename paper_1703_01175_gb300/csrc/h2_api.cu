@@ -717,6 +717,13 @@ h2_status h2_device_status(h2_handle *h)
     int flag = 0;
     h2_status s = h2_split_error_flag(h, &flag);
     if (s != H2_OK) return s;
+    int sflag = 0;
+    s = h2::h2_sym_error_flag(h, &sflag);
+    if (s != H2_OK) return s;
+    if (sflag) {
+        set_error("a bounded wait inside the symmetric-storage kernel ran out");
+        return H2_ERR_TIMEOUT;
+    }
     if (flag) {
         set_error("a bounded wait inside a tensor-core kernel ran out");
         return H2_ERR_TIMEOUT;
@@ -1342,6 +1349,45 @@ extern "C" h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len)
         for (int l = 0; l < h->nlev && s == H2_OK; ++l) s = tune(h->up[l], "up" + std::to_string(l), false);
         for (int l = 0; l < h->nlev && s == H2_OK; ++l) s = tune(h->down[l], "down" + std::to_string(l), false);
     }
+    // symmetric storage: consumer warps of the dual kernel (4: three CTAs per SM, 8: two)
+    auto tune_sym = [&](bool near) -> h2_status {
+        const std::string name = near ? "sym_near" : "sym_couple";
+        int best = h->sym_warps[near ? 1 : 0];
+        float best_us = 1e30f;
+        std::string tried;
+        for (int w : {4, 8}) {
+            h2::sym_set_warps(h, near, w);
+            float ts[3];
+            for (int rep = 0; rep < 4; ++rep) {
+                H2_CUDA(cudaEventRecord(e0, st));
+                H2_CUDA(near ? h2::symnear_run(h, xb, yb, st) : h2::h2_sym_couple(h, coef, st));
+                H2_CUDA(cudaEventRecord(e1, st));
+                H2_CUDA(cudaEventSynchronize(e1));
+                float ms = 0;
+                H2_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) ts[rep - 1] = ms;
+            }
+            std::sort(ts, ts + 3);
+            const float us = ts[1] * 1e3f;
+            const int threads = 32 * (w + 1);
+            tried += (tried.empty() ? "" : ", ") + std::string("\"") + std::to_string(threads) + "\": " +
+                     std::to_string(us);
+            if (us < best_us) {
+                best_us = us;
+                best = w;
+            }
+        }
+        h2::sym_set_warps(h, near, best);
+        js += (first ? "" : ", ") + std::string("\"") + name + "\": {\"threads\": " + std::to_string(32 * (best + 1)) +
+              ", \"us\": " + std::to_string(best_us) + ", \"tried\": {" + tried + "}}";
+        first = false;
+        return H2_OK;
+    };
+    if (s == H2_OK && h->sym_couple) {
+        if (!h->sym) s = h2::h2_sym_init(h);
+        if (s == H2_OK) s = tune_sym(false);
+    }
+    if (s == H2_OK && h->symnear) s = tune_sym(true);
     js += "}";
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1400,7 +1446,11 @@ extern "C" h2_status h2_apply_tuning(h2_handle *h, const char *report)
             pos += strlen(field);
             if (q0 == std::string::npos) return arg_error("h2_apply_tuning: malformed report");
             const std::string key = r.substr(q0 + 1, q1 - q0 - 1);
-            if (field[2] == 't') {
+            if (field[2] == 't' && (key == "sym_couple" || key == "sym_near")) {
+                // symmetric storage: 32 (consumer warps + 1) threads
+                if (val % 32 || !h2::sym_set_warps(h, key == "sym_near", val / 32 - 1))
+                    return arg_error("h2_apply_tuning: bad CTA size for " + key);
+            } else if (field[2] == 't') {
                 auto it = fp.find(key);
                 if (it == fp.end()) return arg_error("h2_apply_tuning: unknown phase " + key);
                 int maxP = 1;

@@ -129,9 +129,9 @@ struct DeviceGuard {
 struct SymState {
     int ntask = 0, ntarget = 0;
     Task *d_tasks = nullptr;
-    Seg *d_segs = nullptr;
+    int32_t *d_xsrc = nullptr;     // per stored column: its input (>= 0: x[.], else coefficient [-. - 1])
     float2 *d_mat = nullptr;
-    int64_t *d_col0 = nullptr;     // per task: first scratch entry
+    int64_t *d_col0 = nullptr;     // per task: first stored column (scratch entry, d_xsrc entry)
     float2 *d_scratch = nullptr;
     int32_t *d_gptr = nullptr;     // per target cluster: range of gcol [ntarget + 1]
     int64_t *d_gcol = nullptr;     // scratch entry of column 0 of each (t, s), t < s
@@ -143,6 +143,9 @@ struct SymState {
     float2 *d_chi = nullptr;       // near field: chi per unknown (tree order)
     float2 *d_rs = nullptr;        // near field: 1 / chi
     float2 *d_xs = nullptr;        // near field: chi x of the current product
+    int *d_err = nullptr;          // set when a bounded wait of the dual kernel ran out
+    uint32_t wait_limit = 1u << 24;
+    int warps = 8;                 // consumer warps of the dual kernel (4 or 8)
 };
 
 // FP64 Arnoldi state of restarted GMRES for R right-hand sides (h2_arnoldi.cu)
@@ -264,6 +267,7 @@ struct h2_handle {
     bool sym_couple = false;          // single-RHS FP32 product: couplings stored once per pair
     h2::SymState *sym = nullptr;      // built on first use (h2_sym.cu)
     h2::SymState *symnear = nullptr;  // near field stored once per leaf pair (h2_sym_near)
+    int sym_warps[2] = {8, 8};        // consumer warps of the dual kernel: couplings, near field (4 or 8)
     // device address of the static scratch array of h2_matvec_noalloc in the
     // context that owns this handle's memory (looked up by the first such call)
     float2 *noalloc_coef = nullptr;
@@ -276,11 +280,15 @@ h2_status h2_ensure_colidx(h2_handle *h);
 void h2_free_split(h2_handle *h);
 namespace h2 {
 h2_status h2_sym_init(h2_handle *h);
+h2_status h2_sym_error_flag(h2_handle *h, int *flag);
 void h2_free_sym(h2_handle *h);
 cudaError_t h2_sym_couple(h2_handle *h, float2 *coef, cudaStream_t st);
 h2_status symnear_init(h2_handle *h, const std::vector<float2> &chi);
 void symnear_free(h2_handle *h);
 cudaError_t symnear_run(h2_handle *h, const float2 *x, float2 *y, cudaStream_t st);
+// consumer warps (4 or 8) of the dual kernel for the couplings (near = false)
+// or the near field; false for another count
+bool sym_set_warps(h2_handle *h, bool near, int warps);
 }  // namespace h2
 h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 *y, int64_t ldy, int nrhs,
                              cudaStream_t st);

@@ -1,4 +1,5 @@
-// Inline-PTX helpers shared by the tcgen05 kernels (h2_umma.cu, h2nn_tc.cu):
+// Inline-PTX helpers shared by the tcgen05 kernels (h2_umma.cu, h2nn_tc.cu)
+// and the bulk-copy pipeline of the symmetric-storage kernel (h2_sym.cu):
 // mbarriers with bounded waits, bulk asynchronous copies, shared-memory
 // matrix descriptors of the canonical no-swizzle K-major layout, the bf16
 // instruction descriptor, the single-CTA MMA and its commit.
@@ -9,6 +10,10 @@
 namespace h2 {
 namespace tc {
 
+// polls of the waits that let copies (and MMAs) in flight finish after a
+// bounded wait ran out, before a CTA releases its shared memory
+constexpr uint32_t kDrainLimit = 1u << 22;
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -17,6 +22,19 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// plain arrival (release at CTA scope): one of the barrier's expected arrivals
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// barrier over the first `count` threads of the CTA (a multiple of 32) on
+// hardware barrier `id` (1..15; 0 is __syncthreads)
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)

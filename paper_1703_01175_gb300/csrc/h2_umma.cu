@@ -53,7 +53,6 @@ constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
 constexpr int CHUNK = MT * 16;        // bytes of one chunk (16 bytes of each of 128 right-hand sides)
 constexpr int GBYTES = 2 * CHUNK;     // bytes of one group of one plane: Re chunk, then Im chunk
 constexpr int XPLANE = (CPS / GRP) * GBYTES;  // bytes of one plane's right-hand-side operand per stage
-constexpr uint32_t kDrainLimit = 1u << 22;  // waits for copies and MMAs in flight after an abort
 
 // shared-memory matrix descriptor of the right-hand-side operand: K-major, no
 // swizzle, 128 rows of 16-byte chunks: 8-row core matrices 128 B apart

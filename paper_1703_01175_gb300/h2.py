@@ -462,7 +462,7 @@ class H2Matrix:
             except (OSError, ValueError):
                 saved = None
             if saved:
-                _check(lib().h2_apply_tuning(self._h, json.dumps(saved).encode()), "h2_apply_tuning")
+                self.apply_tuning(saved)
                 return dict(saved, cached=True)
         buf = ctypes.create_string_buffer(1 << 18)
         rep = {}
@@ -486,6 +486,12 @@ class H2Matrix:
                 json.dump(allc, f)
             os.replace(tmp, cache)
         return rep
+
+    def apply_tuning(self, report: dict):
+        """Apply a report of autotune() (or a part of one) without timing
+        anything (h2_apply_tuning)."""
+        import json
+        _check(lib().h2_apply_tuning(self._h, json.dumps(report).encode()), "h2_apply_tuning")
 
     def configure(self, graphs: bool | None = None, tc_pipeline: bool | None = None):
         """Change the graph and tensor-core pipeline options of the loaded handle."""

@@ -311,6 +311,43 @@ def test_symmetric_couplings_match_oracle(loaded, name):
         B.close()
 
 
+@pytest.mark.parametrize("name", ["cube8", "ragged", "slab", "odd"])
+def test_symmetric_dual_kernel_launch_shapes(loaded, name):
+    """Both launch shapes of the dual kernel (4 consumer warps, three CTAs per
+    SM: 160 threads; 8 warps, two CTAs: 288 threads), for the couplings and
+    the near field: each matches the oracle within 1e-5, the two agree within
+    1e-6 (their slot sums group differently), each replays bitwise; the
+    autotuner reports a choice for both."""
+    import json
+    from paper_1703_01175_gb300 import h2
+    c = cases.get(name)
+    x = synth.random_complex(c.n, 9)
+    xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+    A = h2.H2Matrix(c.arrays(), sym_couple=True)
+    try:
+        ref = c.oracle_matvec(x)
+        for near in (False, True):
+            if near:
+                A.sym_near(c.chi)
+            ys = {}
+            for threads in (160, 288):
+                A.apply_tuning({"sym_couple": {"threads": threads}, "sym_near": {"threads": threads}})
+                y1 = A.matvec(xt).clone()
+                assert torch.equal(y1, A.matvec(xt))
+                assert A.device_status() == 0
+                ys[threads] = y1.cpu().numpy()
+                assert _rel(ys[threads], ref) <= 1e-5
+            assert _rel(ys[160], ys[288]) <= 1e-6
+        rep = A.autotune()
+        assert rep["sym_couple"]["threads"] in (160, 288) and rep["sym_near"]["threads"] in (160, 288)
+        assert set(rep["sym_couple"]["tried"]) == {"160", "288"}
+        with pytest.raises(h2.H2Error):
+            A.apply_tuning({"sym_couple": {"threads": 192}})
+        json.dumps(rep)
+    finally:
+        A.close()
+
+
 def test_symmetric_couplings_reject_asymmetric_data(loaded):
     """A coupling block whose transpose partner differs is refused with
     H2_ERR_STATE on the first product; the handle's full-storage paths and
@@ -336,6 +373,37 @@ def test_symmetric_couplings_reject_asymmetric_data(loaded):
         A.close()
     y = _mat(loaded, "cube8").matvec(x).cpu().numpy()
     assert _rel(y, c.oracle_matvec(x.cpu().numpy().astype(np.complex128))) <= 1e-5
+
+
+def test_symmetric_kernel_timeout_is_reported(loaded):
+    """wait_limit=0 makes the first bounded wait of the symmetric-storage
+    kernel's bulk-copy pipeline run out: the kernel lets its copies land,
+    skips its output and flags the handle (H2_ERR_TIMEOUT), for the couplings
+    and for the near field; the context stays usable."""
+    from paper_1703_01175_gb300 import h2
+    c = cases.get("cube8")
+    x = synth.random_complex(c.n, 46)
+    xt = torch.from_numpy(x.astype(np.complex64)).cuda()
+    A = h2.H2Matrix(c.arrays(), sym_couple=True, wait_limit=0)
+    try:
+        A.matvec(xt)
+        assert A.device_status() == 6   # H2_ERR_TIMEOUT
+    finally:
+        A.close()
+    B = h2.H2Matrix(c.arrays(), sym_couple=True, wait_limit=0)
+    try:
+        B.sym_near(c.chi)
+        B.matvec(xt)
+        assert B.device_status() == 6
+    finally:
+        B.close()
+    C = h2.H2Matrix(c.arrays(), sym_couple=True)
+    try:
+        y = C.matvec(xt).cpu().numpy()
+        assert C.device_status() == 0
+        assert _rel(y, c.oracle_matvec(x)) <= 1e-5
+    finally:
+        C.close()
 
 
 def test_symmetric_couplings_after_reload(loaded, tmp_path):

@@ -71,6 +71,20 @@ __device__ __forceinline__ uint64_t xdesc(uint32_t saddr)
 // group-major plane with ngrp groups per tile (the last one all zero)
 __device__ __forceinline__ int64_t plane_group(int t, int64_t ngrp, int64_t g) { return ((int64_t)t * ngrp + g) * GBYTES; }
 
+// 16 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (one
+// per thread); the caller waits (tcgen05.wait::ld) before using them
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t u[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(u[e]);
+}
+
 __device__ __forceinline__ void split_bf16x8(const float *v, __nv_bfloat16 *hv, __nv_bfloat16 *lv)
 {
 #pragma unroll
@@ -103,9 +117,14 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const UTask tk = tasks[blockIdx.x];
     const int N = tk.n;
-    const uint32_t abytes = (uint32_t)N * 16u * (CPS / 8);  // one plane of the matrix image per stage
+    const uint32_t abytes = (uint32_t)N * 16u * (CPS / 8);  // half of a stage's matrix image (hi or lo rows)
     const uint32_t astride = 2u * (uint32_t)nmax * 16u * (CPS / 8);
     const uint32_t qcol = tcols >> 1;                      // Q accumulator: second half of the columns
+    // N <= 128: the hi and lo rows of the image form one 2N-row operand, four
+    // MMAs per stage instead of six (the right-hand-side operand, re-read from
+    // shared memory by every MMA, is read four times); P and Q then take 2N
+    // columns each, the lo half added in the epilogue
+    const bool fused = N <= 128;
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
     uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
@@ -170,6 +189,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
         }
     } else if (warp == 3 && lane == 0) {
         const uint32_t idesc = idesc_bf16(N);
+        const uint32_t idesc2 = fused ? idesc_bf16(2 * N) : idesc;
         const uint32_t tq = tmem + qcol;
         for (int s = 0; s < tk.nst; ++s) {
             const int b = s % NS;
@@ -180,14 +200,24 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
             consumed = s + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;   // hi, lo planes (Re at +0, Im at +2 KB)
-            const uint32_t aa = smem_u32(sab + b * astride), ab = aa + abytes;
+            // image of the stage: per K chunk, N hi rows then N lo rows (16 B each)
+            const uint32_t aa = smem_u32(sab + b * astride), ab = aa + 16u * (uint32_t)N;
+            const uint64_t bh = kdesc(aa, 32u * (uint32_t)N), bl = kdesc(ab, 32u * (uint32_t)N);
             const uint32_t first = s == 0 ? 0u : 1u;
-            umma(tmem, xdesc(xa), bdesc(aa, N), idesc, first);                 // P: Re hi . hi
-            umma(tmem, xdesc(xa), bdesc(ab, N), idesc, 1u);                    // P: Re hi . lo
-            umma(tmem, xdesc(xb), bdesc(aa, N), idesc, 1u);                    // P: Re lo . hi
-            umma(tq, xdesc(xa + CHUNK), bdesc(aa, N), idesc, first);           // Q: Im hi . hi
-            umma(tq, xdesc(xa + CHUNK), bdesc(ab, N), idesc, 1u);              // Q: Im hi . lo
-            umma(tq, xdesc(xb + CHUNK), bdesc(aa, N), idesc, 1u);              // Q: Im lo . hi
+            if (fused) {
+                // [hi; lo] as one operand of 2N rows: columns [0, N) take hi, [N, 2N) lo
+                umma(tmem, xdesc(xa), bh, idesc2, first);                      // P: Re hi . [hi; lo]
+                umma(tmem, xdesc(xb), bh, idesc, 1u);                          // P: Re lo . hi
+                umma(tq, xdesc(xa + CHUNK), bh, idesc2, first);                // Q: Im hi . [hi; lo]
+                umma(tq, xdesc(xb + CHUNK), bh, idesc, 1u);                    // Q: Im lo . hi
+            } else {
+                umma(tmem, xdesc(xa), bh, idesc, first);                       // P: Re hi . hi
+                umma(tmem, xdesc(xa), bl, idesc, 1u);                          // P: Re hi . lo
+                umma(tmem, xdesc(xb), bh, idesc, 1u);                          // P: Re lo . hi
+                umma(tq, xdesc(xa + CHUNK), bh, idesc, first);                 // Q: Im hi . hi
+                umma(tq, xdesc(xa + CHUNK), bl, idesc, 1u);                    // Q: Im hi . lo
+                umma(tq, xdesc(xb + CHUNK), bh, idesc, 1u);                    // Q: Im lo . hi
+            }
             umma_commit(&empty[b]);
         }
     }
@@ -213,28 +243,29 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
         const int rr = warp * 32 + lane, r = r0 + rr;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
         for (int g = 0; g < N / 16; ++g) {
-            uint32_t pv[16], qv[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(pv[0]), "=r"(pv[1]), "=r"(pv[2]), "=r"(pv[3]), "=r"(pv[4]), "=r"(pv[5]), "=r"(pv[6]),
-                  "=r"(pv[7]), "=r"(pv[8]), "=r"(pv[9]), "=r"(pv[10]), "=r"(pv[11]), "=r"(pv[12]), "=r"(pv[13]),
-                  "=r"(pv[14]), "=r"(pv[15])
-                : "r"(tl + (uint32_t)(16 * g)));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(qv[0]), "=r"(qv[1]), "=r"(qv[2]), "=r"(qv[3]), "=r"(qv[4]), "=r"(qv[5]), "=r"(qv[6]),
-                  "=r"(qv[7]), "=r"(qv[8]), "=r"(qv[9]), "=r"(qv[10]), "=r"(qv[11]), "=r"(qv[12]), "=r"(qv[13]),
-                  "=r"(qv[14]), "=r"(qv[15])
-                : "r"(tl + qcol + (uint32_t)(16 * g)));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float pv[16], qv[16];
+            tmem_ld16(tl + (uint32_t)(16 * g), pv);
+            tmem_ld16(tl + qcol + (uint32_t)(16 * g), qv);
+            if (fused) {
+                // the hi . lo halves, N columns further on
+                float pl[16], ql[16];
+                tmem_ld16(tl + (uint32_t)(N + 16 * g), pl);
+                tmem_ld16(tl + qcol + (uint32_t)(N + 16 * g), ql);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    pv[e] += pl[e];
+                    qv[e] += ql[e];
+                }
+            } else {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
             if (r < nrhs) {
                 float yre[8], yim[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    yre[e] = __uint_as_float(pv[e]) - __uint_as_float(qv[8 + e]);
-                    yim[e] = __uint_as_float(pv[8 + e]) + __uint_as_float(qv[e]);
+                    yre[e] = pv[e] - qv[8 + e];
+                    yim[e] = pv[8 + e] + qv[e];
                 }
                 const int i0 = 8 * g;
                 if (out) {
@@ -269,9 +300,10 @@ size_t umma_ws_smem_bytes(int ns, int nmax)
     return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * (CPS / 8)) + 1024 + 128;
 }
 
-// Pack the bf16-split matrix images of every tile/stage: per stage and plane,
-// two K chunks (8 complex columns each) of N rows of 16 bytes; row 16 q + e is
-// Re of task row row0 + 8 q + e and row 16 q + 8 + e its Im (e < 8). Column pc
+// Pack the bf16-split matrix images of every tile/stage: per stage two K
+// chunks (8 complex columns each), each N hi rows then N lo rows of 16 bytes;
+// row 16 q + e is Re of task row row0 + 8 q + e and row 16 q + 8 + e its Im
+// (e < 8). Column pc
 // of a task starts at element colmap[colmap_off + pc] of mat (-1: padding).
 __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInfo *__restrict__ info,
                                  const int64_t *__restrict__ colmap, const float2 *__restrict__ mat,
@@ -297,9 +329,9 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
         }
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        const int byte = (kk >> 3) * (16 * N) + nr * 16 + (kk & 7) * 2;   // chunk, row, element
+        const int byte = (kk >> 3) * (32 * N) + nr * 16 + (kk & 7) * 2;   // chunk, row, element
         *reinterpret_cast<__nv_bfloat16 *>(img + byte) = hi;
-        *reinterpret_cast<__nv_bfloat16 *>(img + abytes + byte) = lo;
+        *reinterpret_cast<__nv_bfloat16 *>(img + 16 * N + byte) = lo;
     }
 }
 
@@ -623,8 +655,9 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
                 break;
             }
     }
+    // P and Q: 2N columns each for N <= 128 (hi and lo halves), N each above
     uint32_t tcols = 32;
-    while ((int)tcols < 2 * U.nmax) tcols <<= 1;
+    while ((int)tcols < std::min(512, 4 * U.nmax)) tcols <<= 1;
     const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
     __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
 #define H2_UMMA_LAUNCH(NSV)                                                                                  \

@@ -705,6 +705,87 @@ def geometry_leg(geometry, steps, warmup, local_rank):
     return line
 
 
+def geometry_solve_leg(geometry, local_rank, nrhs, restart, maxit, plain_rhs=1):
+    """Solves on one of the paper's scaling geometries at full size: the
+    batched mixed-precision GMRES(m) (split-bf16 tensor-core products, c64-basis
+    Arnoldi with selective reorthogonalisation, double-float-accumulated restart
+    residuals) on `nrhs` random plane waves, run in batches whose Krylov basis
+    fits the free device memory, against plain single-RHS GMRES(m) (FP32
+    products, FP64 Arnoldi, FP64-accumulated restart residuals) on the first
+    `plain_rhs` of them; per right-hand side, with CUDA events."""
+    import torch
+    import synth
+    from paper_1703_01175_gb300 import build, construct_gpu, h2 as h2py
+    build.build_all()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    w = synth.workload(geometry)
+    v = w.voxels
+    t0 = time.time()
+    dh = construct_gpu.build_vie_h2_gpu(v.centres, v.dv, v.eps_r, n_min=w.n_min, eta=w.eta, eps=w.eps,
+                                        device=local_rank)
+    torch.cuda.synchronize(dev)
+    t_build = time.time() - t0
+    perm = dh.perm
+    A = h2py.H2Matrix.from_device(dh, device=local_rank)
+    dh.free()
+    del dh
+    torch.cuda.empty_cache()
+    n = A.n
+    A.autotune()
+    A.autotune(nrhs_tc=min(nrhs, 128), fp32=False)
+    unk = (3 * perm[:, None] + np.arange(3)[None, :]).reshape(-1)
+    Bm = synth.random_plane_waves(v, nrhs, seed=5)[unk]
+    # batch size: the c64 Krylov basis (m + 1 columns), the c128 right-hand sides and solutions and the
+    # per-RHS work vectors within 80 % of the free memory, at most 128 right-hand sides per batch
+    free, _ = torch.cuda.mem_get_info(dev)
+    per_rhs = (restart + 1) * n * 8 + 2 * n * 16 + 8 * n * 16
+    batch = int(max(1, min(128, nrhs, (0.8 * free) // per_rhs)))
+    out = {"geometry": geometry, "n": n, "h2_build_s": round(t_build, 1), "tol": w.tol, "restart": restart,
+           "maxit": maxit, "nrhs": nrhs, "batch": batch, "rhs": "random plane waves (seed 5)"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos, t_new = [], 0.0
+    for c0 in range(0, nrhs, batch):
+        Bt = torch.from_numpy(np.asfortranarray(Bm[:, c0:c0 + batch])).to(dev).t().contiguous().t()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        Xs, info = A.gmres_batched(Bt, tol=w.tol, restart=restart, maxit=maxit, refine=True, prec="splitbf16",
+                                   arnoldi=NEW_ARNOLDI, reorth_eta=NEW_ETA)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_new += e0.elapsed_time(e1)
+        infos += info
+        del Xs, Bt
+        torch.cuda.empty_cache()
+    out["new_batched"] = {"ms_total": t_new, "ms_per_rhs": t_new / nrhs,
+                          "converged": sum(1 for i in infos if i["status"] == 0),
+                          "max_rel_res": max(i["rel_res"] for i in infos),
+                          "mean_iterations": float(np.mean([i["iterations"] for i in infos])),
+                          "max_iterations": int(max(i["iterations"] for i in infos)),
+                          "arnoldi": NEW_ARNOLDI, "reorth_eta": NEW_ETA}
+    plain = []
+    for j in range(plain_rhs):
+        b0 = torch.from_numpy(np.ascontiguousarray(Bm[:, j])).to(dev)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        xs, info = A.gmres(b0, tol=w.tol, restart=restart, maxit=maxit, refine=True, arnoldi="fp64")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain.append({"ms": e0.elapsed_time(e1), "iterations": info[0]["iterations"],
+                      "rel_res": info[0]["rel_res"], "status": info[0]["status"],
+                      "new_iterations_same_rhs": infos[j]["iterations"]})
+        del xs, b0
+    out["plain"] = plain
+    both = all(p["status"] == 0 for p in plain) and out["new_batched"]["converged"] == nrhs
+    out["both_converged"] = both
+    if both:
+        out["new_vs_plain_per_rhs"] = float(np.mean([p["ms"] for p in plain])) / out["new_batched"]["ms_per_rhs"]
+    out["status"] = A.device_status()
+    A.close()
+    return out
+
+
 def learned_leg(wpath, local_rank, dev, stream, nrhs=32, restart=50, maxit=3000):
     """Batched FGMRES with the trained network against plain batched GMRES on
     held-out plane waves (seed 6) of the 48^3 smooth-permittivity cube; the
@@ -869,6 +950,12 @@ def main():
                     help="Arnoldi arithmetic of the --only-gmres cycle")
     ap.add_argument("--geometry", default=None, choices=["slab256", "cube64v", "array4096", "cube48"],
                     help="time one full-size scaling geometry built on the GPU and exit")
+    ap.add_argument("--geometry-solve", default=None, choices=["slab256", "cube64v", "array4096"],
+                    help="time only the batched mixed-precision solve against plain GMRES on this geometry")
+    ap.add_argument("--solve-rhs", type=int, default=0, help="right-hand sides of --geometry-solve (0: the geometry's)")
+    ap.add_argument("--solve-restart", type=int, default=150, help="GMRES restart of --geometry-solve")
+    ap.add_argument("--solve-maxit", type=int, default=3000, help="iteration cap of --geometry-solve")
+    ap.add_argument("--solve-plain-rhs", type=int, default=1, help="plain single-RHS solves of --geometry-solve")
     ap.add_argument("--no-geometries", dest="geometries", action="store_false",
                     help="skip the full-size slab, 64^3 cube and cube-array legs (GPU construction, about 3 minutes)")
     ap.add_argument("--no-plain-batched", dest="plain_batched", action="store_false",
@@ -884,6 +971,12 @@ def main():
         return
     if args.geometry:
         run_geometry(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.geometry_solve:
+        line = geometry_solve_leg(args.geometry_solve, int(os.environ.get("LOCAL_RANK", "0")),
+                                  args.solve_rhs or GEOMETRY_NRHS[args.geometry_solve], args.solve_restart,
+                                  args.solve_maxit, args.solve_plain_rhs)
+        print(json.dumps({"geometry_solve": line}), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

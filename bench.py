@@ -764,6 +764,7 @@ def geometry_solve_leg(geometry, local_rank, nrhs, restart, maxit, plain_rhs=1):
                           "mean_iterations": float(np.mean([i["iterations"] for i in infos])),
                           "max_iterations": int(max(i["iterations"] for i in infos)),
                           "arnoldi": NEW_ARNOLDI, "reorth_eta": NEW_ETA}
+    print(json.dumps({"geometry_solve_partial": out}), file=sys.stderr, flush=True)
     plain = []
     for j in range(plain_rhs):
         b0 = torch.from_numpy(np.ascontiguousarray(Bm[:, j])).to(dev)
@@ -834,6 +835,21 @@ def learned_leg(wpath, local_rank, dev, stream, nrhs=32, restart=50, maxit=3000)
         out["both_converged"] = both
         out["time_ratio_plain_over_learned"] = (out["plain"]["ms_total"] / out["fgmres_learned"]["ms_total"]
                                                 if both else None)
+        # the plain FP32 GMRES(m) of the method on one of the same right-hand sides (single RHS, FP32
+        # products, FP64 Arnoldi, FP64-accumulated restart residuals): the comparator of the full
+        # mixed-precision, batched, learned-preconditioned solve
+        b0 = Bt[:, 0].contiguous()
+        torch.cuda.synchronize(dev)
+        g0.record(stream)
+        xs, info = Aw.gmres(b0, tol=w.tol, restart=restart, maxit=maxit, refine=True, arnoldi="fp64", check=False)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        out["plain_fp32_single"] = {"ms": g0.elapsed_time(g1), "iterations": info[0]["iterations"],
+                                    "rel_res": info[0]["rel_res"], "status": info[0]["status"]}
+        if out["plain_fp32_single"]["status"] == 0 and out["fgmres_learned"]["converged"] == nrhs:
+            out["learned_batched_vs_plain_fp32_per_rhs"] = (out["plain_fp32_single"]["ms"] /
+                                                           out["fgmres_learned"]["ms_per_rhs"])
+        del xs
     finally:
         Aw.close()
         torch.cuda.empty_cache()

@@ -79,8 +79,11 @@ extern "C" h2_status h2_gmres_batched(h2_handle *h, const void *b_, void *x_, in
         for (int r = 0; r < R; ++r)
             if (cudaMemsetAsync(x + (size_t)r * ld, 0, sizeof(double2) * n, st) != cudaSuccess)
                 return (set_error("h2_gmres_batched: cudaMemsetAsync failed"), H2_ERR_CUDA);
-    if ((s = bk_true_residual(h, w, b, ld, x, ld, opts->refine != 0, prec, st)) != H2_OK) return s;
-    if ((s = arn_read(w, st)) != H2_OK) return s;
+    // with x0 = 0 the residual is b itself, already in rr with |b| (no product)
+    if (opts->x0_given) {
+        if ((s = bk_true_residual(h, w, b, ld, x, ld, opts->refine != 0, prec, st)) != H2_OK) return s;
+        if ((s = arn_read(w, st)) != H2_OK) return s;
+    }
     std::vector<char> active(R);
     auto update_active = [&]() {
         int na = 0;

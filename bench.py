@@ -745,6 +745,11 @@ def geometry_solve_leg(geometry, local_rank, nrhs, restart, maxit, plain_rhs=1):
     out = {"geometry": geometry, "n": n, "h2_build_s": round(t_build, 1), "tol": w.tol, "restart": restart,
            "maxit": maxit, "nrhs": nrhs, "batch": batch, "rhs": "random plane waves (seed 5)"}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # untimed call of the same shape: Krylov workspace, tensor-core planes and graphs
+    Bw = torch.from_numpy(np.asfortranarray(Bm[:, :batch])).to(dev).t().contiguous().t()
+    A.gmres_batched(Bw, tol=1e-12, restart=restart, maxit=2, refine=True, prec="splitbf16", arnoldi=NEW_ARNOLDI,
+                    reorth_eta=NEW_ETA, check=False)
+    del Bw
     infos, t_new = [], 0.0
     for c0 in range(0, nrhs, batch):
         Bt = torch.from_numpy(np.asfortranarray(Bm[:, c0:c0 + batch])).to(dev).t().contiguous().t()

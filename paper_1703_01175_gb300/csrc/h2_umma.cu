@@ -120,11 +120,12 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     const uint32_t abytes = (uint32_t)N * 16u * (CPS / 8);  // half of a stage's matrix image (hi or lo rows)
     const uint32_t astride = 2u * (uint32_t)nmax * 16u * (CPS / 8);
     const uint32_t qcol = tcols >> 1;                      // Q accumulator: second half of the columns
-    // N <= 128: the hi and lo rows of the image form one 2N-row operand, four
-    // MMAs per stage instead of six (the right-hand-side operand, re-read from
-    // shared memory by every MMA, is read four times); P and Q then take 2N
-    // columns each, the lo half added in the epilogue
-    const bool fused = N <= 128;
+    // when P and Q fit 2N columns each in the launch's allocation (sized for
+    // N columns each of the widest tile), the hi and lo rows of the image form
+    // one 2N-row operand: four MMAs per stage instead of six (the
+    // right-hand-side operand, re-read from shared memory by every MMA, is
+    // read four times), the lo half added in the epilogue
+    const bool fused = 2u * (uint32_t)N <= qcol;
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
     uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
@@ -655,9 +656,11 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
                 break;
             }
     }
-    // P and Q: 2N columns each for N <= 128 (hi and lo halves), N each above
+    // P and Q: N columns each for the widest tile (2N for the tiles that fit
+    // them, which then fuse their hi and lo operands); a larger allocation
+    // would keep two CTAs from sharing an SM's tensor memory
     uint32_t tcols = 32;
-    while ((int)tcols < std::min(512, 4 * U.nmax)) tcols <<= 1;
+    while ((int)tcols < 2 * U.nmax) tcols <<= 1;
     const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
     __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
 #define H2_UMMA_LAUNCH(NSV)                                                                                  \

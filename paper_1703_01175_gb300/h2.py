@@ -408,15 +408,22 @@ class H2Matrix:
             return x.shape[1], x.stride(1) if x.shape[1] > 1 else self.n
         raise ValueError("x must be (n,) or (n, nrhs) with unit stride along n")
 
-    def matvec_host(self, x: np.ndarray, prec: str = "fp32") -> np.ndarray:
-        """y = A x with host numpy arrays (copies inside the call)."""
+    def matvec_host(self, x: np.ndarray, prec: str = "fp32", out: np.ndarray | None = None) -> np.ndarray:
+        """y = A x with host numpy arrays (copies inside the call); `out`, if
+        given, receives y (same shape, dtype and column-major layout as x;
+        pinned host memory makes both copies direct DMA)."""
         want = np.complex128 if prec in ("fp64acc", "dfacc") else np.complex64
         x = np.asarray(x)
         if x.dtype != want:
             raise TypeError(f"x must be {want}")
         nrhs = 1 if x.ndim == 1 else x.shape[1]
         xf = np.asfortranarray(x)
-        y = np.empty_like(xf, order="F")
+        if out is None:
+            y = np.empty_like(xf, order="F")
+        else:
+            y = out
+            if y.shape != xf.shape or y.dtype != xf.dtype or not y.flags.f_contiguous:
+                raise TypeError("out must match x in shape and dtype and be column-major")
         _check(lib().h2_matvec_host(self._h, xf.ctypes.data, y.ctypes.data, nrhs, self.n, PREC[prec]),
                "h2_matvec_host")
         return y

@@ -29,6 +29,13 @@
 // round-trip through FP32 buffers. The couplings of a cluster and its
 // downward transfer share one tile (their columns concatenated along K), as
 // do the near field and the leaf expansion of a leaf.
+//
+// At most 64 right-hand sides use a packed plane layout: a group is one 2 KB
+// chunk whose rows 0-63 hold the real parts and rows 64-127 the imaginary
+// parts, so one 128-row operand carries both and a single accumulator D holds
+// P in TMEM lanes 0-63 and Q in lanes 64-127 (three MMAs per stage instead of
+// six, half the right-hand-side bytes); the epilogue exchanges the two lane
+// halves through shared memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -57,19 +64,25 @@ constexpr int XPLANE = (CPS / GRP) * GBYTES;  // bytes of one plane's right-hand
 // shared-memory matrix descriptor of the right-hand-side operand: K-major, no
 // swizzle, 128 rows of 16-byte chunks: 8-row core matrices 128 B apart
 // (stride), consecutive K chunks one plane group (4 KB) apart (leading)
-__device__ __forceinline__ uint64_t xdesc(uint32_t saddr)
+__device__ __forceinline__ uint64_t xdesc(uint32_t saddr, uint32_t lbo = GBYTES)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFF);          // start address
-    d |= (uint64_t)(GBYTES >> 4) << 16;               // leading byte offset: next chunk along K
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;       // leading byte offset: next chunk along K
     d |= (uint64_t)(128 >> 4) << 32;                  // stride byte offset: next 8-row group
     d |= (uint64_t)1 << 46;                           // descriptor version (tcgen05)
     return d;                                         // layout type 0: no swizzle
 }
 
 // byte offset of group g (8 complex entries) of right-hand-side tile t in a
-// group-major plane with ngrp groups per tile (the last one all zero)
-__device__ __forceinline__ int64_t plane_group(int t, int64_t ngrp, int64_t g) { return ((int64_t)t * ngrp + g) * GBYTES; }
+// group-major plane with ngrp groups per tile (the last one all zero); gbytes
+// is GBYTES, or CHUNK in the packed layout of at most 64 right-hand sides (one
+// 2 KB chunk per group: rows 0-63 the real parts, rows 64-127 the imaginary
+// parts of right-hand sides 0-63)
+__device__ __forceinline__ int64_t plane_group(int t, int64_t ngrp, int64_t g, uint32_t gbytes = GBYTES)
+{
+    return ((int64_t)t * ngrp + g) * gbytes;
+}
 
 // 16 consecutive FP32 accumulator columns of this warp's 32 TMEM lanes (one
 // per thread); the caller waits (tcgen05.wait::ld) before using them
@@ -111,7 +124,7 @@ __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ groups,
                const uint8_t *__restrict__ images, __nv_bfloat16 *phi, __nv_bfloat16 *plo, int64_t ngrp,
                int nrhs, float2 *__restrict__ out, int64_t ldo, int nmax, uint32_t tcols, int *__restrict__ err,
-               uint32_t wait_limit)
+               uint32_t wait_limit, int packed)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -125,7 +138,11 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     // one 2N-row operand: four MMAs per stage instead of six (the
     // right-hand-side operand, re-read from shared memory by every MMA, is
     // read four times), the lo half added in the epilogue
-    const bool fused = 2u * (uint32_t)N <= qcol;
+    // packed (at most 64 right-hand sides): the real parts of x in TMEM lanes
+    // 0-63 and the imaginary parts in lanes 64-127 of one accumulator D (P in
+    // the first half, Q in the second), three MMAs per stage (two fused)
+    const bool fused = packed ? (N <= 128 && 2u * (uint32_t)N <= tcols) : 2u * (uint32_t)N <= qcol;
+    const uint32_t gbytes = packed ? (uint32_t)CHUNK : (uint32_t)GBYTES;   // bytes of one plane group
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
     uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
@@ -175,17 +192,17 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
             issued = s + 1;
             uint8_t *sx = sxb + b * 2 * XPLANE;
             uint8_t *sa = sab + b * astride;
-            mbar_expect_tx(&full[b], 2 * abytes + 2 * XPLANE);
+            mbar_expect_tx(&full[b], 2 * abytes + 4 * gbytes);
             bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
-            const int64_t oa = plane_group(blockIdx.y, ngrp, ga), ob = plane_group(blockIdx.y, ngrp, gb);
+            const int64_t oa = plane_group(blockIdx.y, ngrp, ga, gbytes), ob = plane_group(blockIdx.y, ngrp, gb, gbytes);
             if (gb == ga + 1) {
-                bulk_g2s(sx, ph + oa, 2 * GBYTES, &full[b]);
-                bulk_g2s(sx + XPLANE, pl + oa, 2 * GBYTES, &full[b]);
+                bulk_g2s(sx, ph + oa, 2 * gbytes, &full[b]);
+                bulk_g2s(sx + XPLANE, pl + oa, 2 * gbytes, &full[b]);
             } else {
-                bulk_g2s(sx, ph + oa, GBYTES, &full[b]);
-                bulk_g2s(sx + GBYTES, ph + ob, GBYTES, &full[b]);
-                bulk_g2s(sx + XPLANE, pl + oa, GBYTES, &full[b]);
-                bulk_g2s(sx + XPLANE + GBYTES, pl + ob, GBYTES, &full[b]);
+                bulk_g2s(sx, ph + oa, gbytes, &full[b]);
+                bulk_g2s(sx + gbytes, ph + ob, gbytes, &full[b]);
+                bulk_g2s(sx + XPLANE, pl + oa, gbytes, &full[b]);
+                bulk_g2s(sx + XPLANE + gbytes, pl + ob, gbytes, &full[b]);
             }
         }
     } else if (warp == 3 && lane == 0) {
@@ -205,7 +222,17 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + 16u * (uint32_t)N;
             const uint64_t bh = kdesc(aa, 32u * (uint32_t)N), bl = kdesc(ab, 32u * (uint32_t)N);
             const uint32_t first = s == 0 ? 0u : 1u;
-            if (fused) {
+            if (packed) {
+                // A = [Re x; Im x] of 64 right-hand sides, K chunks one 2 KB group apart
+                if (fused) {
+                    umma(tmem, xdesc(xa, CHUNK), bh, idesc2, first);           // D: x hi . [hi; lo]
+                    umma(tmem, xdesc(xb, CHUNK), bh, idesc, 1u);               // D: x lo . hi
+                } else {
+                    umma(tmem, xdesc(xa, CHUNK), bh, idesc, first);            // D: x hi . hi
+                    umma(tmem, xdesc(xa, CHUNK), bl, idesc, 1u);               // D: x hi . lo
+                    umma(tmem, xdesc(xb, CHUNK), bh, idesc, 1u);               // D: x lo . hi
+                }
+            } else if (fused) {
                 // [hi; lo] as one operand of 2N rows: columns [0, N) take hi, [N, 2N) lo
                 umma(tmem, xdesc(xa), bh, idesc2, first);                      // P: Re hi . [hi; lo]
                 umma(tmem, xdesc(xb), bh, idesc, 1u);                          // P: Re lo . hi
@@ -237,7 +264,60 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_flag && tk.nst > 0) {
+    if (!abort_flag && tk.nst > 0 && packed) {
+        // lanes 0-63 hold P of right-hand side r = lane, lanes 64-127 its Q;
+        // per group of 8 output rows the Q half goes through shared memory (the
+        // stage buffers are free: every copy landed and every MMA completed)
+        float *xch = reinterpret_cast<float *>(base);     // [64][17]
+        const int rr = warp * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int g = 0; g < N / 16; ++g) {
+            float pv[16];
+            tmem_ld16(tl + (uint32_t)(16 * g), pv);
+            if (fused) {
+                float pl[16];
+                tmem_ld16(tl + (uint32_t)(N + 16 * g), pl);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int e = 0; e < 16; ++e) pv[e] += pl[e];
+            } else {
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            }
+            if (rr >= 64) {
+#pragma unroll
+                for (int e = 0; e < 16; ++e) xch[(rr - 64) * 17 + e] = pv[e];
+            }
+            __syncthreads();
+            if (rr < 64 && rr < nrhs) {
+                float yre[8], yim[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    yre[e] = pv[e] - xch[rr * 17 + 8 + e];
+                    yim[e] = pv[8 + e] + xch[rr * 17 + e];
+                }
+                const int i0 = 8 * g;
+                if (out) {
+                    float2 *o = out + (int64_t)rr * ldo + tk.out_off;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        if (i0 + e < tk.m) o[i0 + e] = make_float2(yre[e], yim[e]);
+                } else if (i0 < tk.m) {
+                    // the group's Re row rr and Im row 64 + rr, hi and lo planes
+                    __align__(16) __nv_bfloat16 hv[8];
+                    __align__(16) __nv_bfloat16 lv[8];
+                    const int64_t goff = plane_group(0, ngrp, (tk.out_off + i0) / GRP, CHUNK) + rr * 16;
+                    uint8_t *bh = reinterpret_cast<uint8_t *>(phi) + goff, *bl = reinterpret_cast<uint8_t *>(plo) + goff;
+                    split_bf16x8(yre, hv, lv);
+                    *reinterpret_cast<uint4 *>(bh) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(bl) = *reinterpret_cast<const uint4 *>(lv);
+                    split_bf16x8(yim, hv, lv);
+                    *reinterpret_cast<uint4 *>(bh + 64 * 16) = *reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(bl + 64 * 16) = *reinterpret_cast<const uint4 *>(lv);
+                }
+            }
+            __syncthreads();
+        }
+    } else if (!abort_flag && tk.nst > 0) {
         // thread = right-hand side r (TMEM lane); per group of 8 output rows,
         // accumulator columns 16 g + e hold the Re rows and 16 g + 8 + e the Im
         // rows of B, in P (real parts of x) and Q (imaginary parts of x)
@@ -345,7 +425,8 @@ __global__ void umma_pack_kernel(const UTask *__restrict__ tasks, const UPackInf
 // and each thread writes one 16-byte chunk row (8 Re or 8 Im values) per plane.
 __global__ void __launch_bounds__(256)
 split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t *__restrict__ pos, int p0, int pend,
-                     int nrhs, __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t ngrp)
+                     int nrhs, __nv_bfloat16 *__restrict__ phi, __nv_bfloat16 *__restrict__ plo, int64_t ngrp,
+                     int packed)
 {
     __shared__ float2 tile[32][33];
     const int d0 = p0 + blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -368,7 +449,9 @@ split_scatter_kernel(const float2 *__restrict__ src, int64_t lds, const int32_t 
     __align__(16) __nv_bfloat16 hv[8];
     __align__(16) __nv_bfloat16 lv[8];
     split_bf16x8(v, hv, lv);
-    const int64_t off = plane_group(r / MT, ngrp, g) + part * CHUNK + (r % MT) * 16;
+    // packed (nrhs <= 64): row part * 64 + r of the group's one chunk
+    const int64_t off = packed ? plane_group(0, ngrp, g, CHUNK) + (part * 64 + r) * 16
+                               : plane_group(r / MT, ngrp, g) + part * CHUNK + (r % MT) * 16;
     *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(phi) + off) = *reinterpret_cast<const uint4 *>(hv);
     *reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(plo) + off) = *reinterpret_cast<const uint4 *>(lv);
 }
@@ -646,6 +729,7 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
                                cudaStream_t st)
 {
     if (U.ntile == 0) return cudaSuccess;
+    const int packed = nrhs <= MT / 2;   // at most 64 right-hand sides: Re and Im in one 128-lane tile
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
     int ns = 2;
     if (S->pipeline) {
@@ -665,7 +749,7 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
     __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
 #define H2_UMMA_LAUNCH(NSV)                                                                                  \
     umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, S->nch, nrhs, out, \
-                                              ldo, U.nmax, tcols, S->d_err, S->wait_limit)
+                                              ldo, U.nmax, tcols, S->d_err, S->wait_limit, packed)
     switch (ns) {
         case 6: H2_UMMA_LAUNCH(6); break;
         case 5: H2_UMMA_LAUNCH(5); break;
@@ -709,10 +793,16 @@ h2_status h2_run_multi_split(h2_handle *h, const float2 *x, int64_t ldx, float2 
     SplitState *S = h->split;
     const int rpad = (nrhs + MT - 1) / MT * MT;
     if ((s = ensure_planes(h, rpad)) != H2_OK) return s;
+    const int packed = nrhs <= MT / 2;
+    if (packed) {
+        // the packed layout's zero group lies where the 128-wide layout keeps data
+        UM_CUDA(cudaMemsetAsync(static_cast<uint8_t *>(S->phi) + (S->nch - 1) * (int64_t)CHUNK, 0, CHUNK, st));
+        UM_CUDA(cudaMemsetAsync(static_cast<uint8_t *>(S->plo) + (S->nch - 1) * (int64_t)CHUNK, 0, CHUNK, st));
+    }
     dim3 g((unsigned)((S->np_x + 31) / 32), (nrhs + 31) / 32);
     split_scatter_kernel<<<g, 256, 0, st>>>(x, ldx, S->d_xpos, 0, (int)S->np_x, nrhs,
                                             reinterpret_cast<__nv_bfloat16 *>(S->phi),
-                                            reinterpret_cast<__nv_bfloat16 *>(S->plo), S->nch);
+                                            reinterpret_cast<__nv_bfloat16 *>(S->plo), S->nch, packed);
     UM_CUDA(cudaGetLastError());
     // upward pass: forward transforms of the leaves, then level by level
     UM_CUDA(launch_umma(S->upleaf, S, nrhs, nullptr, 0, st));

@@ -151,6 +151,29 @@ def test_splitbf16_tensor_cores_match_oracle(loaded, name, R, pipeline):
         assert colerr.max() <= 1e-4
 
 
+def test_splitbf16_packed_and_wide_layouts_alternate(loaded):
+    """At most 64 right-hand sides use the packed plane layout (real and
+    imaginary parts in the two halves of one 128-lane tile), more use the
+    128-wide one; alternating them on one handle (32, 128, 32, 100, 1) keeps
+    every product within eps of the oracle, and the packed columns agree with
+    the same columns of a wide product within eps."""
+    from oracle import h2mv
+    c = cases.get("cube12")
+    A = _mat(loaded, "cube12")
+    X = synth.random_complex(c.n, 15, cols=128)
+    Y_or = h2mv.h2_dense(c.hZ) @ X
+    wide = None
+    for R in (32, 128, 32, 100, 1):
+        Y = A.matvec(_colmajor(X[:, :R]), prec="splitbf16").cpu().numpy().reshape(c.n, R)
+        assert A.device_status() == 0
+        colerr = np.linalg.norm(Y - Y_or[:, :R], axis=0) / np.linalg.norm(Y_or[:, :R], axis=0)
+        assert colerr.max() <= 1e-4, (R, float(colerr.max()))
+        if R == 128:
+            wide = Y
+        elif wide is not None:
+            assert _rel(Y, wide[:, :R]) <= 1e-4
+
+
 def test_graph_replay_and_autotune(loaded):
     """The captured-graph product equals the directly launched one bitwise;
     after autotuning the launch shapes the product still matches the oracle."""

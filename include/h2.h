@@ -214,7 +214,7 @@ h2_status h2_autotune(h2_handle *h, char *report, int32_t report_len);
  * Autotune the split-bf16 tensor-core product for nrhs right-hand sides: for
  * every phase (leaf forward transforms, upward transfers per level, merged
  * coupling / downward tiles per level, merged near-field / leaf-expansion
- * tiles) time each pipeline depth that fits in shared memory (2 ... 6
+ * tiles) time each pipeline depth that fits in shared memory (2 ... 8
  * stages) with CUDA events and keep the fastest. Writes a JSON report
  * ("tc_<phase>": {"ns": depth, "us": time, "tiles": count, "tried": {...}})
  * into report[0..report_len) when report is not NULL. Allocates the
@@ -228,7 +228,7 @@ h2_status h2_autotune_tc(h2_handle *h, int32_t nrhs, char *report, int32_t repor
  * from an earlier run on the same GPU and operator shape) without timing
  * anything: "<phase>": {"threads": N} sets a CTA size (a multiple of 32 in
  * [rows / 2, 1024]; 160 or 288 for "sym_couple" and "sym_near"),
- * "<phase>": {"ns": N} a tensor-core pipeline depth (0 ... 6; 0 = deepest
+ * "<phase>": {"ns": N} a tensor-core pipeline depth (0 ... 8; 0 = deepest
  * that fits). H2_ERR_ARG for an unknown phase or a bad value. Drops captured
  * graphs.
  */

@@ -1464,7 +1464,7 @@ extern "C" h2_status h2_apply_tuning(h2_handle *h, const char *report)
                     if (s != H2_OK) return s;
                     tc_seen = true;
                 }
-                if (val < 0 || val > 6) return arg_error("h2_apply_tuning: bad pipeline depth for " + key);
+                if (val < 0 || val > 8) return arg_error("h2_apply_tuning: bad pipeline depth for " + key);
                 if (!h2_split_set_ns(h, key, val)) return arg_error("h2_apply_tuning: unknown phase " + key);
             }
         }

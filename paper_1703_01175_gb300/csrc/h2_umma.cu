@@ -60,6 +60,7 @@ constexpr int MT = 128;               // right-hand sides per tile (TMEM lanes)
 constexpr int CHUNK = MT * 16;        // bytes of one chunk (16 bytes of each of 128 right-hand sides)
 constexpr int GBYTES = 2 * CHUNK;     // bytes of one group of one plane: Re chunk, then Im chunk
 constexpr int XPLANE = (CPS / GRP) * GBYTES;  // bytes of one plane's right-hand-side operand per stage
+constexpr int NSMAX = 8;              // deepest pipeline (16 NSMAX + 4 bytes of barriers fit the 256 reserved)
 
 // shared-memory matrix descriptor of the right-hand-side operand: K-major, no
 // swizzle, 128 rows of 16-byte chunks: 8-row core matrices 128 B apart
@@ -119,12 +120,12 @@ __device__ __forceinline__ void split_bf16x8(const float *v, __nv_bfloat16 *hv, 
 // the real parts, three into Q from the imaginary parts) and commits them to
 // the stage's `empty` barrier. All four warps then read both accumulators out
 // of tensor memory and combine them.
-template <int NS>
+template <int NS, bool packed>
 __global__ void __launch_bounds__(UT, 1)
 umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ groups,
                const uint8_t *__restrict__ images, __nv_bfloat16 *phi, __nv_bfloat16 *plo, int64_t ngrp,
                int nrhs, float2 *__restrict__ out, int64_t ldo, int nmax, uint32_t tcols, int *__restrict__ err,
-               uint32_t wait_limit, int packed)
+               uint32_t wait_limit)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -142,9 +143,12 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     // 0-63 and the imaginary parts in lanes 64-127 of one accumulator D (P in
     // the first half, Q in the second), three MMAs per stage (two fused)
     const bool fused = packed ? (N <= 128 && 2u * (uint32_t)N <= tcols) : 2u * (uint32_t)N <= qcol;
-    const uint32_t gbytes = packed ? (uint32_t)CHUNK : (uint32_t)GBYTES;   // bytes of one plane group
+    constexpr uint32_t gbytes = packed ? (uint32_t)CHUNK : (uint32_t)GBYTES;   // bytes of one plane group
+    // per stage: the hi and lo right-hand-side operands (XST bytes; the packed
+    // layout needs half), then the matrix image
+    constexpr uint32_t XST = packed ? XPLANE : 2 * XPLANE, XLO = XST / 2;
     uint8_t *sxb = base;                                   // NS x (hi, lo) X planes
-    uint8_t *sab = base + NS * 2 * XPLANE;                 // NS x (hi, lo) matrix planes
+    uint8_t *sab = base + NS * XST;                        // NS x (hi, lo) matrix planes
     uint64_t *bars = reinterpret_cast<uint64_t *>(sab + NS * astride);
     uint64_t *full = bars;
     uint64_t *empty = bars + NS;
@@ -190,19 +194,19 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
                 break;
             }
             issued = s + 1;
-            uint8_t *sx = sxb + b * 2 * XPLANE;
+            uint8_t *sx = sxb + b * XST;
             uint8_t *sa = sab + b * astride;
             mbar_expect_tx(&full[b], 2 * abytes + 4 * gbytes);
             bulk_g2s(sa, images + tk.img_off + (int64_t)s * 2 * abytes, 2 * abytes, &full[b]);
             const int64_t oa = plane_group(blockIdx.y, ngrp, ga, gbytes), ob = plane_group(blockIdx.y, ngrp, gb, gbytes);
             if (gb == ga + 1) {
                 bulk_g2s(sx, ph + oa, 2 * gbytes, &full[b]);
-                bulk_g2s(sx + XPLANE, pl + oa, 2 * gbytes, &full[b]);
+                bulk_g2s(sx + XLO, pl + oa, 2 * gbytes, &full[b]);
             } else {
                 bulk_g2s(sx, ph + oa, gbytes, &full[b]);
                 bulk_g2s(sx + gbytes, ph + ob, gbytes, &full[b]);
-                bulk_g2s(sx + XPLANE, pl + oa, gbytes, &full[b]);
-                bulk_g2s(sx + XPLANE + gbytes, pl + ob, gbytes, &full[b]);
+                bulk_g2s(sx + XLO, pl + oa, gbytes, &full[b]);
+                bulk_g2s(sx + XLO + gbytes, pl + ob, gbytes, &full[b]);
             }
         }
     } else if (warp == 3 && lane == 0) {
@@ -217,12 +221,12 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
             }
             consumed = s + 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t xa = smem_u32(sxb + b * 2 * XPLANE), xb = xa + XPLANE;   // hi, lo planes (Re at +0, Im at +2 KB)
+            const uint32_t xa = smem_u32(sxb + b * XST), xb = xa + XLO;   // hi, lo planes (wide: Re at +0, Im at +2 KB)
             // image of the stage: per K chunk, N hi rows then N lo rows (16 B each)
             const uint32_t aa = smem_u32(sab + b * astride), ab = aa + 16u * (uint32_t)N;
             const uint64_t bh = kdesc(aa, 32u * (uint32_t)N), bl = kdesc(ab, 32u * (uint32_t)N);
             const uint32_t first = s == 0 ? 0u : 1u;
-            if (packed) {
+            if constexpr (packed) {
                 // A = [Re x; Im x] of 64 right-hand sides, K chunks one 2 KB group apart
                 if (fused) {
                     umma(tmem, xdesc(xa, CHUNK), bh, idesc2, first);           // D: x hi . [hi; lo]
@@ -264,7 +268,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!abort_flag && tk.nst > 0 && packed) {
+    if (packed && !abort_flag && tk.nst > 0) {
         // lanes 0-63 hold P of right-hand side r = lane, lanes 64-127 its Q;
         // per group of 8 output rows the Q half goes through shared memory (the
         // stage buffers are free: every copy landed and every MMA completed)
@@ -317,7 +321,7 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
             }
             __syncthreads();
         }
-    } else if (!abort_flag && tk.nst > 0) {
+    } else if (!packed && !abort_flag && tk.nst > 0) {
         // thread = right-hand side r (TMEM lane); per group of 8 output rows,
         // accumulator columns 16 g + e hold the Re rows and 16 g + 8 + e the Im
         // rows of B, in P (real parts of x) and Q (imaginary parts of x)
@@ -376,9 +380,10 @@ umma_ws_kernel(const UTask *__restrict__ tasks, const int32_t *__restrict__ grou
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
-size_t umma_ws_smem_bytes(int ns, int nmax)
+size_t umma_ws_smem_bytes(int ns, int nmax, bool packed = false)
 {
-    return (size_t)ns * (2 * XPLANE + 2 * (size_t)nmax * 16 * (CPS / 8)) + 1024 + 128;
+    // + alignment of the base to 1 KB, + the barriers (2 NS x 8 B) and the TMEM address slot
+    return (size_t)ns * ((packed ? 1 : 2) * XPLANE + 2 * (size_t)nmax * 16 * (CPS / 8)) + 1024 + 256;
 }
 
 // Pack the bf16-split matrix images of every tile/stage: per stage two K
@@ -680,19 +685,27 @@ static h2_status split_init(h2_handle *h)
         // dynamic shared memory limit = opt-in per-block maximum minus the kernels' static shared memory
         int optin = 0;
         UM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device));
-        cudaFuncAttributes fa{};
-        UM_CUDA(cudaFuncGetAttributes(&fa, umma_ws_kernel<2>));
-        S->dyn_smem_limit = optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        cudaFuncAttributes fa{}, fp{};
+        UM_CUDA(cudaFuncGetAttributes(&fa, umma_ws_kernel<2, false>));
+        UM_CUDA(cudaFuncGetAttributes(&fp, umma_ws_kernel<2, true>));
+        const int stat = (int)std::max(fa.sharedSizeBytes, fp.sharedSizeBytes);
+        S->dyn_smem_limit = optin > stat ? (size_t)optin - stat : 0;
         if (umma_ws_smem_bytes(2, nmax) > S->dyn_smem_limit) {
             set_error("split-bf16: two pipeline stages of the widest tile exceed shared memory");
             return H2_ERR_STATE;
         }
         const int lim = (int)S->dyn_smem_limit;
-        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-        UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+#define H2_UMMA_ATTR(NSV)                                                                                   \
+    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<NSV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)); \
+    UM_CUDA(cudaFuncSetAttribute(umma_ws_kernel<NSV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))
+        H2_UMMA_ATTR(2);
+        H2_UMMA_ATTR(3);
+        H2_UMMA_ATTR(4);
+        H2_UMMA_ATTR(5);
+        H2_UMMA_ATTR(6);
+        H2_UMMA_ATTR(7);
+        H2_UMMA_ATTR(8);
+#undef H2_UMMA_ATTR
     }
     UM_CUDA(cudaMalloc(&S->d_err, sizeof(int)));
     UM_CUDA(cudaMemset(S->d_err, 0, sizeof(int)));
@@ -733,9 +746,9 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
     dim3 grid(U.ntile, (nrhs + MT - 1) / MT);
     int ns = 2;
     if (S->pipeline) {
-        const int want = U.ns > 0 ? std::min(6, U.ns) : std::min(6, std::max(2, U.maxnst));
+        const int want = U.ns > 0 ? std::min(NSMAX, U.ns) : std::min(NSMAX, std::max(2, U.maxnst));
         for (int c = want; c > 2; --c)
-            if (umma_ws_smem_bytes(c, U.nmax) <= S->dyn_smem_limit) {
+            if (umma_ws_smem_bytes(c, U.nmax, packed) <= S->dyn_smem_limit) {
                 ns = c;
                 break;
             }
@@ -745,18 +758,29 @@ static cudaError_t launch_umma(const UPhase &U, const SplitState *S, int nrhs, f
     // would keep two CTAs from sharing an SM's tensor memory
     uint32_t tcols = 32;
     while ((int)tcols < 2 * U.nmax) tcols <<= 1;
-    const size_t sm = umma_ws_smem_bytes(ns, U.nmax);
+    const size_t sm = umma_ws_smem_bytes(ns, U.nmax, packed);
     __nv_bfloat16 *phi = reinterpret_cast<__nv_bfloat16 *>(S->phi), *plo = reinterpret_cast<__nv_bfloat16 *>(S->plo);
 #define H2_UMMA_LAUNCH(NSV)                                                                                  \
-    umma_ws_kernel<NSV><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, S->nch, nrhs, out, \
-                                              ldo, U.nmax, tcols, S->d_err, S->wait_limit, packed)
-    switch (ns) {
-        case 6: H2_UMMA_LAUNCH(6); break;
-        case 5: H2_UMMA_LAUNCH(5); break;
-        case 4: H2_UMMA_LAUNCH(4); break;
-        case 3: H2_UMMA_LAUNCH(3); break;
-        default: H2_UMMA_LAUNCH(2); break;
+    umma_ws_kernel<NSV, PK><<<grid, UT, sm, st>>>(U.d_tasks, U.d_chunks, U.d_images, phi, plo, S->nch, nrhs, \
+                                                  out, ldo, U.nmax, tcols, S->d_err, S->wait_limit)
+#define H2_UMMA_SWITCH                     \
+    switch (ns) {                          \
+        case 8: H2_UMMA_LAUNCH(8); break;  \
+        case 7: H2_UMMA_LAUNCH(7); break;  \
+        case 6: H2_UMMA_LAUNCH(6); break;  \
+        case 5: H2_UMMA_LAUNCH(5); break;  \
+        case 4: H2_UMMA_LAUNCH(4); break;  \
+        case 3: H2_UMMA_LAUNCH(3); break;  \
+        default: H2_UMMA_LAUNCH(2); break; \
     }
+    if (packed) {
+        constexpr bool PK = true;
+        H2_UMMA_SWITCH
+    } else {
+        constexpr bool PK = false;
+        H2_UMMA_SWITCH
+    }
+#undef H2_UMMA_SWITCH
 #undef H2_UMMA_LAUNCH
     return cudaGetLastError();
 }
@@ -876,8 +900,8 @@ h2_status h2_split_autotune(h2_handle *h, int nrhs, std::string &js, bool &first
         float best_us = 1e30f;
         std::string tried;
         const int old_ns = U.ns;
-        for (int c = 2; c <= 6 && e == cudaSuccess; ++c) {
-            if (umma_ws_smem_bytes(c, U.nmax) > S->dyn_smem_limit) break;
+        for (int c = 2; c <= NSMAX && e == cudaSuccess; ++c) {
+            if (umma_ws_smem_bytes(c, U.nmax, nrhs <= MT / 2) > S->dyn_smem_limit) break;
             if (c > 2 && c > U.maxnst) break;   // deeper than the longest tile's stages buys nothing
             U.ns = c;
             float ts[3] = {0, 0, 0};

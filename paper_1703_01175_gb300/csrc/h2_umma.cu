@@ -34,8 +34,9 @@
 // chunk whose rows 0-63 hold the real parts and rows 64-127 the imaginary
 // parts, so one 128-row operand carries both and a single accumulator D holds
 // P in TMEM lanes 0-63 and Q in lanes 64-127 (three MMAs per stage instead of
-// six, half the right-hand-side bytes); the epilogue exchanges the two lane
-// halves through shared memory.
+// six, half the right-hand-side bytes, so deeper pipelines fit); the epilogue
+// exchanges the two lane halves through shared memory. The layout is a
+// template parameter of the kernel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -171,6 +171,18 @@ def _blas_threads():
         return os.cpu_count()
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over the ranks of the process group (the slowest
+    replica's time per step); the value itself for one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -286,11 +298,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(dev)
         barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
 
     if args.only_matvec:
         A.close()

@@ -216,7 +216,8 @@ def workload(name: str) -> Workload:
     array4096: 4096 cubes of 4^3 voxels on the x axis, pitch 0.5, eps_r 2.54.
     cube16r  : 16^3 cube, side 1, eps_r ~ U[2,6] (seed 2): the training geometry
                of the learned preconditioner (cube32's voxel size and eps_r law).
-    Smaller grids "cubeNN" (uniform eps_r 4, side NN/16) are test cases.
+    Smaller grids "cubeNN" (uniform eps_r 4, side NN/16) are test cases, and
+    "arrayNNN" is the array4096 family with NNN cubes (the 1-D scaling series).
     """
     h16 = 1.0 / 16.0
     if name == "cube8":
@@ -241,6 +242,9 @@ def workload(name: str) -> Workload:
         # same voxel size and eps_r distribution as cube32, 16^3 voxels
         v = random_eps_grid((16, 16, 16), (h16,) * 3, 2.0, 6.0, seed=2, name=name)
         return Workload(v, 96, 1.0, 1e-4, 1, None, 1e-4)
+    if name.startswith("array") and name[5:].isdigit():
+        v = cube_array_1d(int(name[5:]), 4, h16, 0.5, 2.54, name)
+        return Workload(v, 96, 1.0, 1e-4, 256, 8, 1e-4)
     if name.startswith("cube") and name[4:].isdigit():
         m = int(name[4:])
         v = uniform_grid((m, m, m), (h16,) * 3, 4.0, name)

@@ -58,7 +58,7 @@ struct UTask {
     int32_t m;          // complex rows in this tile (<= 128)
     int32_t n;          // real MMA N = 2 * round_up(m, 8)
     int32_t nst;        // K stages of 16 complex columns
-    int64_t img_off;    // byte offset of stage 0's image (hi plane, then lo plane)
+    int64_t img_off;    // byte offset of stage 0's image (per K chunk: N hi rows, then N lo rows)
     int32_t chunk_off;  // first entry in the group table (2 plane positions per stage)
     int32_t pad_;
 };
